@@ -1,0 +1,421 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 Block-Parallel IDA* solver.
+
+Metric: 15-puzzle node expansions/s (and instances/s), plain vs batched,
+with every integer result equal to the CPU oracle's.
+
+Workload (default): 100 seeded uniformly random solvable 15-puzzle boards
+(``inputs.perms15_100``; a stand-in for the paper's 100-instance benchmark
+set), Manhattan heuristic, all-optimal-solutions mode (the final iteration
+is searched to completion, so node counts are order-free). One step solves
+all 100 boards:
+
+* plain (headline ``value``): one solve call per board, as in the paper's
+  one-instance-per-run experiments;
+* batched (``batched``): all 100 boards in one solve call.
+
+Expansions are the nodes expanded over all iterations of all instances.
+Inputs are resident in HBM when a timed step starts; L2 is flushed (a
+256 MiB write) between steps. ``e2e`` repeats the plain step through the
+host-buffer path: pinned boards copied to the device and every result copied
+back inside the timed region.
+
+Multi-GPU: instances are independent, so each rank solves its own copy of
+the workload with no collective on the data path (replicas; weak scaling).
+
+``--impl reference`` times the CPU oracle (plain sequential IDA*, one thread
+per instance, all host cores) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1705_02843_gb300 import inputs as I  # noqa: E402
+
+METRIC = "15-puzzle node expansions/s & instances/s, batched vs plain, oracle-exact"
+UNIT = "expansions/s"
+WORKLOAD_DESC = ("perms15_100: 100 seeded uniformly random solvable 15-puzzle boards "
+                 "(seeds 1001-1100), Manhattan distance, all-optimal-solutions mode")
+
+# Warp instructions issued per node expanded inside k_search<4,512>, from
+# ncu (smsp__inst_executed.sum / nodes) on the one-board capture recorded
+# in profiles/k_search_15puzzle.txt. None until measured.
+INSTR_PER_EXPANSION = None
+# DRAM bytes per k_search launch from the same capture, scaled to the mean
+# launch of this workload; None when not measured for the current kernel.
+TRAFFIC_PER_LAUNCH = None
+
+
+def golden_path(name):
+    return os.path.join(ROOT, "tests", "golden", name + ".json")
+
+
+def load_golden(name):
+    p = golden_path(name)
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        return {r["index"]: r for r in json.load(f)["instances"]}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread is not None:
+                self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    """CPU oracle arm: rank 0 only; other ranks exit without work."""
+    if rank != 0:
+        return
+    import oracle
+
+    insts = I.WORKLOADS[args.workload]()
+    gold = load_golden(args.workload)
+    sample, cores = pick_cpu_sample(insts, gold, args.cpu_sample_nodes)
+    tiles = I.tiles_array([insts[i] for i in sample])
+    times, nodes_tot = [], 0
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        res = oracle.solve_batch(4, tiles, count_all=True, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            nodes_tot = sum(r.total_nodes for r in res)
+    t = statistics.mean(times)
+    value = nodes_tot / t
+    desc = "%d of %d boards (the cheapest by stored oracle node count), %d expansions" % (
+        len(sample), len(insts), nodes_tot)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "mode": "CPU oracle, one thread per board"},
+        "instances_per_s": len(sample) / t,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def pick_cpu_sample(insts, gold, budget_nodes):
+    cores = os.cpu_count() or 1
+    if gold:
+        order = sorted(gold, key=lambda i: sum(gold[i]["nodes"]))
+        sample, acc = [], 0
+        for i in order:
+            c = sum(gold[i]["nodes"])
+            if acc + c > budget_nodes and sample:
+                break
+            sample.append(i)
+            acc += c
+        return sample, cores
+    return list(range(min(8, len(insts)))), cores
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="perms15_100", choices=["perms15_100"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-nodes", type=float, default=1.5e9)
+    ap.add_argument("--profile-case", type=int, default=None, metavar="IDX",
+                    help="solve board IDX alone with one search pass per iteration (for ncu "
+                         "captures: the final iteration's k_search launch is number iters-1), "
+                         "print its statistics and exit")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world, rank, local = dist_setup()
+
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+
+    from paper_1705_02843_gb300 import bpida
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    insts = I.WORKLOADS[args.workload]()
+    if args.profile_case is not None:
+        x = insts[args.profile_case]
+        b = torch.from_numpy(I.packed_array([x]).view(np.int64)).to(dev)
+        for rep in range(2):
+            s = bpida.solve(b, 4, bpida.make_config(4, exit_fraction_pct=100))
+            torch.cuda.synchronize(dev)
+        h = s.to_host()[0]
+        st = bpida.last_stats()
+        print(json.dumps({"profile_case": args.profile_case, "status": s.status, "length": h["length"],
+                          "iters": h["iters"], "nodes": h["nodes"], "stats": st}), flush=True)
+        return
+    n = len(insts)
+    packed = I.packed_array(insts)
+    boards = torch.from_numpy(packed.view(np.int64)).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    bpida.set_timing(True)
+
+    def plain_step():
+        sols, agg = [], {"search_ms": 0.0, "search_nodes": 0, "passes": 0, "launches": 0}
+        for i in range(n):
+            s = bpida.solve(boards[i:i + 1], 4)
+            if s.status != bpida.OK:
+                raise RuntimeError("solve failed: " + bpida.status_str(s.status))
+            st = bpida.last_stats()
+            for k in agg:
+                agg[k] += st[k]
+            sols.append(s)
+        return sols, agg
+
+    def batched_step():
+        s = bpida.solve(boards, 4)
+        if s.status != bpida.OK:
+            raise RuntimeError("solve failed: " + bpida.status_str(s.status))
+        st = bpida.last_stats()
+        return [s], {k: st[k] for k in ("search_ms", "search_nodes", "passes", "launches")}
+
+    def expansions(sols):
+        tot = 0
+        for s in sols:
+            tot += int(s.nodes.cpu().numpy().view(np.uint64).sum())
+        return tot
+
+    def timed(step_fn, k, warm):
+        for _ in range(warm):
+            step_fn()
+        torch.cuda.synchronize(dev)
+        if pg:
+            pg.barrier()
+        ms, aggs, sols = [], [], None
+        for _ in range(k):
+            flush.fill_(1)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sols, agg = step_fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+            aggs.append(agg)
+        torch.cuda.synchronize(dev)
+        if pg:
+            pg.barrier()
+        return ms, aggs, sols
+
+    # parity of this run's results against the stored oracle results
+    gold = load_golden(args.workload)
+    sols, _ = plain_step()
+    checked = mismatched = 0
+    if gold:
+        for i, s in enumerate(sols):
+            if i in gold:
+                h = s.to_host()[0]
+                g = gold[i]
+                checked += 1
+                if h["length"] != g["length"] or h["nodes"] != g["nodes"] or "".join(map(str, h["moves"])) != g["moves"]:
+                    mismatched += 1
+    exp_per_step = expansions(sols)
+
+    with ClockSampler(local) as clk:
+        ms_plain, agg_plain, _ = timed(plain_step, args.steps, args.warmup)
+        ms_batch, agg_batch, bsols = timed(batched_step, args.steps, 1)
+    clocks = clk.summary()
+    if expansions(bsols) != exp_per_step:
+        raise RuntimeError("batched and plain expansions differ")
+
+    # end to end through the host-buffer path (pinned boards, results back)
+    host_boards = torch.from_numpy(packed.view(np.int64)).pin_memory()
+    ml, mi = bpida.max_len(4), bpida.max_iters(4)
+    h2d = host_boards.numel() * 8
+    d2h = n * (4 + ml + 8 * mi + 4 + 4)
+    host_out = {k: torch.empty(sz, dtype=dt).pin_memory() for k, sz, dt in (
+        ("len", n, torch.int32), ("moves", n * ml, torch.uint8), ("nodes", n * mi, torch.int64),
+        ("iters", n, torch.int32), ("status", n, torch.int32))}
+
+    def e2e_step():
+        dboards = host_boards.to(dev, non_blocking=True)
+        sols = []
+        for i in range(n):
+            s = bpida.solve(dboards[i:i + 1], 4)
+            if s.status != bpida.OK:
+                raise RuntimeError(bpida.status_str(s.status))
+            sols.append(s)
+        host_out["len"].copy_(torch.cat([s.length for s in sols]), non_blocking=True)
+        host_out["moves"].copy_(torch.cat([s.moves.reshape(-1) for s in sols]), non_blocking=True)
+        host_out["nodes"].copy_(torch.cat([s.nodes.reshape(-1) for s in sols]), non_blocking=True)
+        host_out["iters"].copy_(torch.cat([s.iters for s in sols]), non_blocking=True)
+        host_out["status"].copy_(torch.cat([s.inst_status for s in sols]), non_blocking=True)
+        return sols, {}
+
+    ms_e2e, _, _ = timed(e2e_step, max(1, args.steps), 1)
+    e2e_exp = int(host_out["nodes"].numpy().view(np.uint64).sum())
+    if e2e_exp != exp_per_step:
+        raise RuntimeError("end-to-end expansions differ")
+
+    def mx(v):
+        if pg is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
+
+    t_plain = mx(sum(ms_plain)) / 1e3
+    t_batch = mx(sum(ms_batch)) / 1e3
+    t_e2e = mx(sum(ms_e2e)) / 1e3
+    k = args.steps
+    value = world * exp_per_step * k / t_plain
+    inst_s = world * n * k / t_plain
+    b_value = world * exp_per_step * k / t_batch
+    e2e_value = world * exp_per_step * len(ms_e2e) / t_e2e
+
+    # roofline of the dominant kernel (k_search), from the plain step's own
+    # CUDA-event timings of every k_search launch
+    s_ms = sum(a["search_ms"] for a in agg_plain)
+    s_nodes = sum(a["search_nodes"] for a in agg_plain)
+    s_launch = sum(a["passes"] for a in agg_plain)
+    launches = sum(a["launches"] for a in agg_plain) // k
+    sms = bpida.last_stats()["sm_count"]
+    f_mhz = clocks["sm_mhz"] or 1455.0
+    peak = sms * 4 * f_mhz * 1e6 / 1e9  # warp-instructions issued, G/s
+    roof = None
+    if INSTR_PER_EXPANSION:
+        achieved = s_nodes * INSTR_PER_EXPANSION / (s_ms / 1e3) / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
+                "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH,
+                "kernel": "k_search<4,512>", "instr_per_expansion": INSTR_PER_EXPANSION,
+                "launch_ms_mean": s_ms / max(s_launch, 1),
+                "expansions_per_s_in_kernel": s_nodes / (s_ms / 1e3),
+                "peak_basis": "%d SMs x 4 schedulers x %.0f MHz median SM clock sampled during the run" % (sms, f_mhz)}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": peak, "unit": "Gwarp-inst/s", "frac": None,
+                "traffic": None, "kernel": "k_search<4,512>",
+                "expansions_per_s_in_kernel": s_nodes / (s_ms / 1e3) if s_ms else None}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        sample, cores = pick_cpu_sample(insts, gold, args.cpu_sample_nodes)
+        t0 = time.perf_counter()
+        res = oracle.solve_batch(4, I.tiles_array([insts[i] for i in sample]), count_all=True, nthreads=cores)
+        dt = time.perf_counter() - t0
+        cn = sum(r.total_nodes for r in res)
+        cpu = {"value": cn / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d of %d boards (cheapest by stored oracle node count), %d expansions, %.1f s" % (
+                   len(sample), n, cn, dt),
+               "instances_per_s": len(sample) / dt}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": k,
+            "warmup": args.warmup, "ms_per_step": t_plain * 1e3 / k, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "mode": "plain: one solve call per board",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "flushed between steps (256 MiB write)"},
+            "instances_per_s": inst_s,
+            "expansions_per_step": exp_per_step,
+            "batched": {"value": b_value, "unit": UNIT, "instances_per_s": world * n * k / t_batch,
+                        "ms_per_step": t_batch * 1e3 / k, "mode": "all 100 boards in one solve call"},
+            "parity": {"checked": checked, "mismatched": mismatched,
+                       "against": "stored oracle results (length, per-iteration nodes, first solution)"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": t_e2e * 1e3 / len(ms_e2e)},
+            "roofline": roof,
+            "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
+                       "reasons": clocks["reasons"]},
+            "gpu_launches": launches * k,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

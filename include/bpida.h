@@ -1,0 +1,140 @@
+/*
+ * bpida.h — C ABI of the GB300 (sm_103a) Block-Parallel IDA* solver.
+ *
+ * The solver finds optimal solutions of sliding-tile puzzles (8-, 15- and
+ * 24-puzzle) with IDA* under the Manhattan distance heuristic, running the
+ * f-limited depth-first search of every iteration on the GPU with a warp
+ * per subtree (Horie & Fukunaga, "Block-Parallel IDA* for GPUs",
+ * Section 5, Algorithm 1). All integer results are exact.
+ *
+ * Conventions (every buffer and result uses them):
+ *   - positions are row-major 0 .. W*W-1; the goal has tile t at position t
+ *     and the blank (tile 0) at position 0;
+ *   - a move is the direction the blank travels: 0 = up, 1 = left,
+ *     2 = right, 3 = down; the inverse of the previous move is never
+ *     applied;
+ *   - a node is counted ("expanded") when it is taken off the search stack
+ *     with f <= limit; the root and goal nodes count; a goal is not
+ *     expanded further;
+ *   - the first f-limit is h(start); each later limit is the smallest f of
+ *     the children pruned in the previous iteration (Algorithm 1);
+ *   - with count_all = 1 the final iteration is searched to completion, as
+ *     in the all-optimal-solutions experiment of Section 6, so its node
+ *     count does not depend on the order in which nodes are expanded.
+ *
+ * Board packing (device memory, read-only to the library):
+ *   W = 3 or 4: one uint64_t per board, tile at position p in bits [4p, 4p+4).
+ *   W = 5:      two uint64_t per board (low word first) forming a 128-bit
+ *               integer with the tile at position p in bits [5p, 5p+5).
+ *
+ * Streams and ownership: every pointer argument of the solve calls is
+ * DEVICE memory owned by the caller; the library keeps no reference after
+ * returning. Work is issued on `stream`; the call returns once the results
+ * are written (the threshold loop reads small control words back to the
+ * host). The library owns a per-device workspace that it grows on demand
+ * and frees in bpida_release_workspace().
+ *
+ * Errors: arguments the host can check are rejected synchronously with
+ * BPIDA_EINVAL before any work is issued. Per-instance problems are
+ * reported in out_status[i] and do not stop the other instances. The
+ * library never calls __trap() or a device assert.
+ */
+#ifndef BPIDA_H
+#define BPIDA_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BPIDA_OK = 0,
+    BPIDA_EINVAL = 1,   /* bad argument, or a board that is not a permutation
+                           or not in the goal's parity class (unsolvable) */
+    BPIDA_ENOMEM = 2,   /* device workspace or work-queue capacity exceeded */
+    BPIDA_ESTACK = 3,   /* reserved: search stack bound exceeded */
+    BPIDA_EBUDGET = 4,  /* node budget exhausted before a solution */
+    BPIDA_ETIMEOUT = 5, /* reserved: a bounded device wait gave up */
+    BPIDA_ECUDA = 6,    /* a CUDA runtime call failed */
+    BPIDA_ELIMIT = 7,   /* solution longer than bpida_max_len(width) */
+    BPIDA_EINTERNAL = 8 /* an internal consistency check failed */
+} bpida_status;
+
+typedef struct {
+    int width;            /* 3, 4 or 5 (8-, 15-, 24-puzzle); 0 means 4 */
+    int count_all;        /* 1 = final iteration searched to completion */
+    int split_target;     /* max frontier records per instance; 0 = auto */
+    int warps_per_block;  /* search kernel block size in warps; 0 = auto */
+    int stack_entries;    /* per-warp shared-memory stack, 0 = auto
+                             (one of 256, 512, 1024) */
+    int exit_fraction_pct;/* percentage of warps that must have run out of
+                             work before busy warps hand their stacks back
+                             for redistribution; 0 = auto */
+    int min_rounds;       /* rounds a warp runs before it may hand back its
+                             stack; 0 = auto */
+    uint64_t node_budget; /* per instance, over all iterations; 0 = none */
+} bpida_config;
+
+typedef struct {
+    int steps;              /* threshold steps issued (all instances) */
+    int passes;             /* search kernel launches */
+    uint64_t records;       /* frontier records produced by the splitter */
+    uint64_t handed_back;   /* stack entries handed back between passes */
+    uint64_t search_nodes;  /* nodes expanded inside the search kernel */
+    double search_ms;       /* sum of search kernel durations (CUDA events
+                               on the launching stream); 0 unless timed */
+    int grid_blocks;        /* search kernel grid */
+    int block_threads;      /* search kernel block */
+    int sm_count;
+    int launches;           /* kernels launched by the call */
+    uint64_t spills;        /* stack overflows handed to the next pass */
+    int max_handed_back;    /* largest hand-back queue of one pass */
+} bpida_stats;
+
+/* Upper bounds used to size the per-instance output rows. */
+int bpida_max_len(int width);    /* moves per solution row */
+int bpida_max_iters(int width);  /* iterations per node-count row */
+
+/*
+ * Solve n boards with the default configuration (15-puzzle, count_all = 1).
+ *   boards             device, n words (packing above)
+ *   out_len            device, n ints: optimal length, -1 if none
+ *   out_moves          device, n * bpida_max_len(4) bytes; row i holds the
+ *                      lexicographically first optimal solution (moves in
+ *                      the order up < left < right < down), zero-filled
+ *   out_nodes_per_iter device, n * bpida_max_iters(4) uint64: nodes
+ *                      expanded in each iteration, zero-filled
+ * Returns BPIDA_OK if every instance was solved, otherwise the first error
+ * code met (per-instance codes are available through bpida_solve_ex).
+ */
+bpida_status bpida_solve(const uint64_t *boards, int n, int *out_len, uint8_t *out_moves,
+                         uint64_t *out_nodes_per_iter, void *stream);
+
+/*
+ * As bpida_solve, with a configuration and per-instance outputs:
+ *   out_num_iters device, n ints: iterations run (may be NULL)
+ *   out_status    device, n ints: bpida_status of each instance (may be NULL)
+ * Row widths are bpida_max_len(cfg->width) and bpida_max_iters(cfg->width).
+ */
+bpida_status bpida_solve_ex(const bpida_config *cfg, const uint64_t *boards, int n, int *out_len,
+                            uint8_t *out_moves, uint64_t *out_nodes_per_iter, int *out_num_iters,
+                            int *out_status, void *stream);
+
+/* Statistics of the last solve call made by this host thread. If `timed` is
+ * set before a call (bpida_set_timing(1)), search kernel durations are
+ * recorded with CUDA events on the launching stream. */
+void bpida_set_timing(int on);
+void bpida_get_stats(bpida_stats *out);
+
+/* Free the calling device's workspace. */
+void bpida_release_workspace(void);
+
+const char *bpida_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BPIDA_H */

@@ -1,0 +1,199 @@
+"""Python binding of the bpida C ABI (``include/bpida.h``).
+
+Argument marshalling only: every step of the search runs in the CUDA
+kernels of ``libbpida.so``. PyTorch supplies device memory and the stream.
+There is no CPU fallback: if the library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import List, Optional
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbpida.so")
+
+OK, EINVAL, ENOMEM, ESTACK, EBUDGET, ETIMEOUT, ECUDA, ELIMIT, EINTERNAL = range(9)
+
+EXPORTS = (
+    "bpida_max_len", "bpida_max_iters", "bpida_solve", "bpida_solve_ex", "bpida_set_timing",
+    "bpida_get_stats", "bpida_release_workspace", "bpida_status_str",
+)
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("width", ctypes.c_int),
+        ("count_all", ctypes.c_int),
+        ("split_target", ctypes.c_int),
+        ("warps_per_block", ctypes.c_int),
+        ("stack_entries", ctypes.c_int),
+        ("exit_fraction_pct", ctypes.c_int),
+        ("min_rounds", ctypes.c_int),
+        ("node_budget", ctypes.c_uint64),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("steps", ctypes.c_int),
+        ("passes", ctypes.c_int),
+        ("records", ctypes.c_uint64),
+        ("handed_back", ctypes.c_uint64),
+        ("search_nodes", ctypes.c_uint64),
+        ("search_ms", ctypes.c_double),
+        ("grid_blocks", ctypes.c_int),
+        ("block_threads", ctypes.c_int),
+        ("sm_count", ctypes.c_int),
+        ("launches", ctypes.c_int),
+        ("spills", ctypes.c_uint64),
+        ("max_handed_back", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load():
+    """Load libbpida.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                "libbpida.so is not built (run `python -c 'import __graft_entry__ as g; g.build()'`)")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        lib.bpida_max_len.argtypes = [ctypes.c_int]
+        lib.bpida_max_len.restype = ctypes.c_int
+        lib.bpida_max_iters.argtypes = [ctypes.c_int]
+        lib.bpida_max_iters.restype = ctypes.c_int
+        lib.bpida_solve.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp]
+        lib.bpida_solve.restype = ctypes.c_int
+        lib.bpida_solve_ex.argtypes = [ctypes.POINTER(Config), vp, ctypes.c_int, vp, vp, vp, vp, vp, vp]
+        lib.bpida_solve_ex.restype = ctypes.c_int
+        lib.bpida_set_timing.argtypes = [ctypes.c_int]
+        lib.bpida_set_timing.restype = None
+        lib.bpida_get_stats.argtypes = [ctypes.POINTER(Stats)]
+        lib.bpida_get_stats.restype = None
+        lib.bpida_release_workspace.argtypes = []
+        lib.bpida_release_workspace.restype = None
+        lib.bpida_status_str.argtypes = [ctypes.c_int]
+        lib.bpida_status_str.restype = ctypes.c_char_p
+        _lib = lib
+    return _lib
+
+
+def max_len(width: int) -> int:
+    return load().bpida_max_len(width)
+
+
+def max_iters(width: int) -> int:
+    return load().bpida_max_iters(width)
+
+
+def status_str(code: int) -> str:
+    return load().bpida_status_str(code).decode()
+
+
+def set_timing(on: bool) -> None:
+    load().bpida_set_timing(1 if on else 0)
+
+
+def last_stats() -> dict:
+    s = Stats()
+    load().bpida_get_stats(ctypes.byref(s))
+    return s.as_dict()
+
+
+def release_workspace() -> None:
+    load().bpida_release_workspace()
+
+
+@dataclass
+class Solution:
+    status: int                    # call status
+    length: torch.Tensor           # int32 (n,)
+    moves: torch.Tensor            # uint8 (n, max_len)
+    nodes: torch.Tensor            # int64 (n, max_iters) (uint64 bit pattern)
+    iters: torch.Tensor            # int32 (n,)
+    inst_status: torch.Tensor      # int32 (n,)
+
+    def to_host(self):
+        """Per-instance dicts with Python ints (moves trimmed to the length)."""
+        L = self.length.cpu().tolist()
+        mv = self.moves.cpu().numpy()
+        nd = self.nodes.cpu().numpy().view("uint64")
+        it = self.iters.cpu().tolist()
+        stt = self.inst_status.cpu().tolist()
+        out = []
+        for i in range(len(L)):
+            out.append({
+                "status": stt[i], "length": L[i],
+                "moves": [int(x) for x in mv[i, :max(L[i], 0)]],
+                "nodes": [int(x) for x in nd[i, :it[i]]],
+                "iters": it[i],
+            })
+        return out
+
+
+def make_config(width: int = 4, split_target: int = 0, warps_per_block: int = 0,
+                stack_entries: int = 0, exit_fraction_pct: int = 0, min_rounds: int = 0,
+                node_budget: int = 0) -> Config:
+    return Config(width, 1, split_target, warps_per_block, stack_entries, exit_fraction_pct,
+                  min_rounds, node_budget)
+
+
+def solve(boards: torch.Tensor, width: int = 4, config: Optional[Config] = None,
+          stream: Optional[torch.cuda.Stream] = None) -> Solution:
+    """Solve packed boards already on the GPU.
+
+    ``boards``: CUDA int64 tensor, shape (n,) for width 3/4, (n, 2) for 5,
+    holding the packed words (bit pattern of the uint64 layout in bpida.h).
+    Outputs are allocated on the same device; the call runs on ``stream``
+    (default: the current stream).
+    """
+    lib = load()
+    if not boards.is_cuda:
+        raise ValueError("boards must be a CUDA tensor")
+    if boards.dtype not in (torch.int64, getattr(torch, "uint64", torch.int64)):
+        raise ValueError("boards must be a 64-bit integer tensor")
+    boards = boards.contiguous()
+    n = boards.shape[0]
+    if width == 5 and (boards.dim() != 2 or boards.shape[1] != 2):
+        raise ValueError("width-5 boards must have shape (n, 2)")
+    cfg = config if config is not None else make_config(width)
+    cfg.width = width
+    dev = boards.device
+    ml, mi = lib.bpida_max_len(width), lib.bpida_max_iters(width)
+    out_len = torch.empty(n, dtype=torch.int32, device=dev)
+    out_moves = torch.empty((n, ml), dtype=torch.uint8, device=dev)
+    out_nodes = torch.empty((n, mi), dtype=torch.int64, device=dev)
+    out_iters = torch.empty(n, dtype=torch.int32, device=dev)
+    out_status = torch.empty(n, dtype=torch.int32, device=dev)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    with torch.cuda.device(dev):
+        rc = lib.bpida_solve_ex(ctypes.byref(cfg), boards.data_ptr(), n, out_len.data_ptr(),
+                                out_moves.data_ptr(), out_nodes.data_ptr(), out_iters.data_ptr(),
+                                out_status.data_ptr(), s.cuda_stream)
+    return Solution(rc, out_len, out_moves, out_nodes, out_iters, out_status)
+
+
+def solve_packed_host(packed, width: int = 4, config: Optional[Config] = None,
+                      device: str = "cuda") -> List[dict]:
+    """Convenience: numpy/list of packed words on the host -> host results."""
+    import numpy as np
+
+    arr = np.ascontiguousarray(np.asarray(packed, dtype=np.uint64)).view(np.int64)
+    t = torch.from_numpy(arr).to(device)
+    sol = solve(t, width, config)
+    torch.cuda.synchronize()
+    res = sol.to_host()
+    for r in res:
+        r["call_status"] = sol.status
+    return res

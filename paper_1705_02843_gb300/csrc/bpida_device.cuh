@@ -1,0 +1,917 @@
+// Device side of the GB300 Block-Parallel IDA* solver.
+//
+// Method (Horie & Fukunaga, "Block-Parallel IDA* for GPUs"):
+//   * Algorithm 1, BPDFS: a group of threads shares one stack of open
+//     nodes; each repetition pops several nodes at once, tests them for the
+//     goal, generates children with f = g + cost + h, pushes those with
+//     f <= limit (linearizable put) and keeps min f of the rest as f_next.
+//     Here the group is one warp, one node per lane; children are pushed
+//     with __ballot_sync/__popc slot reservation into a shared-memory ring.
+//   * Algorithm 1, BPIDA*: a root set is built, the first limit is decided,
+//     and each iteration searches every root's subtree in parallel. Here the
+//     root set is rebuilt every iteration by k_split (a breadth-first,
+//     order-preserving expansion of the top levels of the same depth-first
+//     tree, without duplicate detection, so node counts stay those of
+//     sequential IDA*), the first limit is h(start), and the next limit is
+//     the smallest pruned f.
+//   * Section 5's static load balancing (per-root work estimates from the
+//     previous iteration) is replaced by a work queue consumed by persistent
+//     warps plus hand-back: when enough warps have run dry, busy warps write
+//     their open nodes back to a queue and the next pass redistributes them.
+//
+// Nothing in this file waits on another warp, block or kernel: every loop
+// is bounded by the work it consumes, so no kernel can hang.
+#pragma once
+#include <stdint.h>
+#include <limits.h>
+#include <cuda_runtime.h>
+
+namespace bp {
+
+typedef unsigned __int128 u128;
+
+template <int W> struct Geo;
+template <> struct Geo<3> {
+    typedef uint64_t B;
+    static constexpr int N = 9, BITS = 4, MAXLEN = 32, MAXIT = 17;
+};
+template <> struct Geo<4> {
+    typedef uint64_t B;
+    static constexpr int N = 16, BITS = 4, MAXLEN = 80, MAXIT = 41;
+};
+template <> struct Geo<5> {
+    typedef u128 B;
+    static constexpr int N = 25, BITS = 5, MAXLEN = 208, MAXIT = 105;
+};
+
+template <int W>
+__host__ __device__ __forceinline__ typename Geo<W>::B goal_board()
+{
+    typedef typename Geo<W>::B B;
+    B g = 0;
+#pragma unroll
+    for (int p = 0; p < Geo<W>::N; ++p)
+        g |= (B)(unsigned)p << (Geo<W>::BITS * p);
+    return g;
+}
+
+template <int W>
+__host__ __device__ __forceinline__ unsigned tile_at(typename Geo<W>::B b, int p)
+{
+    return (unsigned)(b >> (Geo<W>::BITS * p)) & ((1u << Geo<W>::BITS) - 1u);
+}
+
+// ---- node metadata (32 bits) ----
+//  bits  0..4   blank position
+//  bits  5..7   last move (0..3), 4 = none
+//  bits  8..15  slack = limit - g - h  (>= 0 for every stored node)
+//  bits 16..20  records: depth below the split root; stack: origin slot
+//  bit  21      records: goal found above the split depth (a leaf)
+__host__ __device__ __forceinline__ uint32_t m_blank(uint32_t m) { return m & 31u; }
+__host__ __device__ __forceinline__ uint32_t m_last(uint32_t m) { return (m >> 5) & 7u; }
+__host__ __device__ __forceinline__ int m_slack(uint32_t m) { return (int)((m >> 8) & 255u); }
+__host__ __device__ __forceinline__ uint32_t m_hi(uint32_t m) { return (m >> 16) & 31u; }
+static constexpr uint32_t M_LEAF = 1u << 21;
+static constexpr uint32_t M_NODE_MASK = 0xFFFFu;
+static constexpr uint32_t LAST_NONE = 4u;
+__host__ __device__ __forceinline__ uint32_t m_make(uint32_t blank, uint32_t last, uint32_t slack)
+{
+    return blank | (last << 5) | (slack << 8);
+}
+
+// A frontier / queue record.
+template <int W> struct Rec {
+    typename Geo<W>::B b;
+    uint32_t meta;
+    uint32_t inst;    // instance index
+    uint32_t origin;  // index of the frontier record this node descends from
+    uint32_t pm;      // moves from the split root, 2 bits each, first lowest
+};
+
+// ---- Manhattan move table ----
+// For blank position p and move m, word e[p][m]:
+//   bit 0        the move keeps the blank on the board
+//   bit t (t>0)  sliding tile t from the blank's new position into p moves
+//                it away from its goal cell (h rises by 1; else h falls by 1)
+template <int W> struct MoveLut { uint32_t e[Geo<W>::N][4]; };
+
+// Per-lane view of one table row. W <= 4: the four 16-bit masks of a row
+// are packed into one 64-bit word, so a warp reads the 16 rows from 32
+// distinct banks. W = 5: one 16-byte row.
+template <int W, bool Narrow = (W <= 4)> struct LutRow;
+template <int W> struct LutRow<W, true> {
+    uint64_t v;
+    __device__ __forceinline__ bool legal(int m) const { return (v >> (16 * m)) & 1u; }
+    __device__ __forceinline__ bool away(int m, unsigned t) const { return (v >> (16 * m + t)) & 1u; }
+};
+template <int W> struct LutRow<W, false> {
+    uint4 v;
+    __device__ __forceinline__ uint32_t w(int m) const { return m == 0 ? v.x : m == 1 ? v.y : m == 2 ? v.z : v.w; }
+    __device__ __forceinline__ bool legal(int m) const { return w(m) & 1u; }
+    __device__ __forceinline__ bool away(int m, unsigned t) const { return (w(m) >> t) & 1u; }
+};
+
+template <int W> struct SharedLut {
+    static constexpr int BYTES = (W <= 4) ? 8 * 16 : 16 * 25;
+    // fills shared memory from the kernel-parameter copy (block-wide)
+    __device__ static void load(unsigned char *dst, const MoveLut<W> &src)
+    {
+        if (W <= 4) {
+            uint64_t *d = (uint64_t *)dst;
+            for (int p = threadIdx.x; p < Geo<W>::N; p += blockDim.x) {
+                uint64_t v = 0;
+                for (int m = 0; m < 4; ++m)
+                    v |= (uint64_t)(src.e[p][m] & 0xFFFFu) << (16 * m);
+                d[p] = v;
+            }
+        } else {
+            uint4 *d = (uint4 *)dst;
+            for (int p = threadIdx.x; p < Geo<W>::N; p += blockDim.x)
+                d[p] = make_uint4(src.e[p][0], src.e[p][1], src.e[p][2], src.e[p][3]);
+        }
+    }
+    __device__ static __forceinline__ LutRow<W> row(const unsigned char *base, int p)
+    {
+        LutRow<W> r;
+        if constexpr (W <= 4)
+            r.v = ((const uint64_t *)base)[p];
+        else
+            r.v = ((const uint4 *)base)[p];
+        return r;
+    }
+};
+
+// Blank displacement of move m: up, left, right, down.
+template <int W> __device__ __forceinline__ int move_off(int m)
+{
+    return m == 0 ? -W : m == 1 ? -1 : m == 2 ? 1 : W;
+}
+
+// ---- shared control block ----
+struct Ctrl {
+    int n_in;         // records in this pass's input queue
+    int head;         // next input record to take
+    int out_count;    // records handed back during this pass
+    int exited;       // warps that found the input exhausted
+    int err;          // error bits (ERR_*)
+    int n_active;     // problems in this step
+    int n_next;       // problems for the next step
+    int pad;
+    unsigned long long records_total;
+    unsigned long long handed_back_total;
+    unsigned long long search_nodes_total;  // nodes popped by k_search
+    unsigned long long spills;               // stack overflows handed back
+    int max_out;                             // largest hand-back of one pass
+    int pad2;
+};
+static constexpr int ERR_QUEUE = 1;      // hand-back queue full
+static constexpr int ERR_INTERNAL = 2;   // consistency check failed
+
+// ---- per-instance state ----
+enum { MODE_COUNT = 0, MODE_PATH = 1, MODE_DONE = 2 };
+template <int W> struct InstState {
+    typename Geo<W>::B start;
+    typename Geo<W>::B root;     // root of the next split
+    uint32_t start_meta;         // blank | none | 0
+    uint32_t root_meta;          // blank | last | slack
+    int h0;
+    int limit;
+    int it;                      // index of the current iteration
+    int rows;                    // node-count rows written
+    int path_len;
+    int mode;
+    int status;
+    int length;
+    uint32_t target;             // frontier records wanted from the next split
+    uint32_t pad;
+    unsigned long long cum_nodes;
+    unsigned long long solutions;
+};
+
+struct Counters {
+    unsigned long long *search_nodes;  // nodes popped inside the search kernel
+    unsigned long long *split_nodes;   // nodes expanded by the splitter
+    int *fnext_off;                    // min over pruned children of f - limit
+    unsigned long long *goals;         // goal nodes popped
+    unsigned *goal_origin;             // smallest origin of a goal-bearing record
+};
+
+struct Tune {
+    int min_rounds;      // rounds before a warp may hand its stack back
+    int exit_threshold;  // warps that must have run dry first
+    int nodes_per_record;
+    int target_cap;      // per-problem frontier cap
+    int target_path;     // frontier records wanted for a path step
+    int growth;          // expected node growth per iteration (x)
+};
+
+// ---------------------------------------------------------------------
+// Warp-level helpers
+// ---------------------------------------------------------------------
+static constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ int warp_min_int(int v)
+{
+#pragma unroll
+    for (int d = 16; d; d >>= 1)
+        v = min(v, __shfl_xor_sync(FULL, v, d));
+    return v;
+}
+__device__ __forceinline__ unsigned warp_min_u32(unsigned v)
+{
+#pragma unroll
+    for (int d = 16; d; d >>= 1)
+        v = min(v, __shfl_xor_sync(FULL, v, d));
+    return v;
+}
+
+// Block-wide exclusive scan of small non-negative ints (blockDim <= 1024).
+__device__ __forceinline__ int block_exclusive_scan(int v, int *warp_sums, int *total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    int x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int y = __shfl_up_sync(FULL, x, d);
+        if (lane >= d)
+            x += y;
+    }
+    if (lane == 31)
+        warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int y = __shfl_up_sync(FULL, s, d);
+            if (lane >= d)
+                s += y;
+        }
+        if (lane < nw)
+            warp_sums[lane] = s;  // inclusive
+    }
+    __syncthreads();
+    int before = (wid > 0 ? warp_sums[wid - 1] : 0) + x - v;
+    *total = warp_sums[nw - 1];
+    __syncthreads();
+    return before;
+}
+
+// ---------------------------------------------------------------------
+// Search kernel: persistent warps, one subtree group per warp.
+// ---------------------------------------------------------------------
+template <int W> struct SearchArgs {
+    const Rec<W> *in;
+    Rec<W> *out;
+    int out_cap;
+    Ctrl *ctrl;
+    Counters cnt;
+    Tune tune;
+    MoveLut<W> lut;
+};
+
+template <int W, int S>
+__device__ __forceinline__ void hand_back_stack(const SearchArgs<W> &a, typename Geo<W>::B *sb,
+                                                uint32_t *sm, int from, int k, unsigned inst,
+                                                unsigned my_origin, int lane)
+{
+    if (k <= 0)
+        return;
+    int base = 0;
+    if (lane == 0)
+        base = atomicAdd(&a.ctrl->out_count, k);
+    base = __shfl_sync(FULL, base, 0);
+    const bool fits = base + k <= a.out_cap;
+    if (!fits) {
+        if (lane == 0)
+            atomicOr(&a.ctrl->err, ERR_QUEUE);
+    }
+    for (int j0 = 0; j0 < k; j0 += 32) {
+        const int j = j0 + lane;
+        const bool ok = j < k;
+        const int si = (from + j) & (S - 1);
+        uint32_t m = ok ? sm[si] : 0u;
+        unsigned o = __shfl_sync(FULL, my_origin, m_hi(m));
+        if (ok && fits) {
+            Rec<W> r;
+            r.b = sb[si];
+            r.meta = m & M_NODE_MASK;
+            r.inst = inst;
+            r.origin = o;
+            r.pm = 0;
+            a.out[base + j] = r;
+        }
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void hand_back_records(const SearchArgs<W> &a, int from, int to, int lane)
+{
+    const int k = to - from;
+    if (k <= 0)
+        return;
+    int base = 0;
+    if (lane == 0)
+        base = atomicAdd(&a.ctrl->out_count, k);
+    base = __shfl_sync(FULL, base, 0);
+    if (base + k > a.out_cap) {
+        if (lane == 0)
+            atomicOr(&a.ctrl->err, ERR_QUEUE);
+        return;
+    }
+    for (int j = lane; j < k; j += 32)
+        a.out[base + j] = a.in[from + j];
+}
+
+template <int W, int S>
+__global__ void k_search(const SearchArgs<W> a)
+{
+    typedef typename Geo<W>::B B;
+    constexpr int BITS = Geo<W>::BITS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char *lut = smem;
+    SharedLut<W>::load(lut, a.lut);
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    B *sb = (B *)(smem + SharedLut<W>::BYTES) + (size_t)warp * S;
+    uint32_t *sm = (uint32_t *)((B *)(smem + SharedLut<W>::BYTES) + (size_t)(blockDim.x >> 5) * S) +
+                   (size_t)warp * S;
+    const unsigned lt = (1u << lane) - 1u;
+    const B GOAL = goal_board<W>();
+    const int n_in = a.ctrl->n_in;
+    const int total_warps = gridDim.x * (blockDim.x >> 5);
+    const int chunk = max(1, min(32, n_in / (total_warps * 4)));
+    int rounds = 0;
+    bool stop = false;
+
+    for (;;) {
+        int h = 0;
+        if (lane == 0)
+            h = atomicAdd(&a.ctrl->head, chunk);
+        h = __shfl_sync(FULL, h, 0);
+        if (h >= n_in)
+            break;
+        const int end = min(h + chunk, n_in);
+        int i = h;
+        while (i < end) {
+            // take the run of records [i, i+cnt) that belong to one instance
+            const int idx = i + lane;
+            const bool v = idx < end;
+            Rec<W> r;
+            if (v)
+                r = a.in[idx];
+            const unsigned inst = v ? r.inst : 0xffffffffu;
+            const unsigned inst0 = __shfl_sync(FULL, inst, 0);
+            const unsigned same = __ballot_sync(FULL, v && inst == inst0);
+            const int cnt = (same == FULL) ? 32 : (__ffs(~same) - 1);
+            const unsigned my_origin = v ? r.origin : 0u;
+            if (lane < cnt) {
+                sb[lane] = r.b;
+                sm[lane] = (r.meta & M_NODE_MASK) | ((uint32_t)lane << 16);
+            }
+            int top = cnt, bot = 0;
+            __syncwarp();
+            unsigned long long nodes = 0;
+            int fmin = INT_MAX;
+
+            while (top != bot) {
+                const int size = top - bot;
+                const int n = min(32, size);
+                if (size + 3 * n > S) {
+                    // keep room for up to 4n children (an instance root has
+                    // four): hand the oldest entries to the next pass. After
+                    // it, size <= max(n, S/2) and size + 3n <= S for S >= 256.
+                    const int k = min(size - n, S / 2);
+                    if (lane == 0)
+                        atomicAdd(&a.ctrl->spills, 1ull);
+                    hand_back_stack<W, S>(a, sb, sm, bot, k, inst0, my_origin, lane);
+                    bot += k;
+                    __syncwarp();
+                }
+                const bool act = lane < n;
+                const int si = (top - n + lane) & (S - 1);
+                B b = 0;
+                uint32_t mt = 0;
+                if (act) {
+                    b = sb[si];
+                    mt = sm[si];
+                }
+                top -= n;
+                nodes += (unsigned long long)n;
+                __syncwarp();
+
+                const bool goal = act && (b == GOAL);
+                const unsigned gmask = __ballot_sync(FULL, goal);
+                if (gmask) {
+                    unsigned o = __shfl_sync(FULL, my_origin, m_hi(mt));
+                    o = warp_min_u32(goal ? o : 0xffffffffu);
+                    if (lane == 0) {
+                        atomicAdd(&a.cnt.goals[inst0], (unsigned long long)__popc(gmask));
+                        atomicMin(&a.cnt.goal_origin[inst0], o);
+                    }
+                }
+                const bool expand = act && !goal;
+                const int p = (int)m_blank(mt);
+                const int last = (int)m_last(mt);
+                const int s = m_slack(mt);
+                const uint32_t slotbits = mt & (31u << 16);
+                const LutRow<W> e = SharedLut<W>::row(lut, p);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const bool legal = expand && e.legal(m) && (last != 3 - m);
+                    const int np = legal ? p + move_off<W>(m) : p;
+                    const unsigned t = tile_at<W>(b, np);
+                    // h changes by +1 (away from goal cell) or -1, g by +1:
+                    // the child's slack is s - 2 or s
+                    const int s2 = e.away(m, t) ? s - 2 : s;
+                    const bool push = legal && s2 >= 0;
+                    if (legal && s2 < 0)
+                        fmin = min(fmin, -s2);
+                    const B x = (B)t;
+                    const B child = b + (x << (BITS * p)) - (x << (BITS * np));
+                    const uint32_t cm = (uint32_t)np | ((uint32_t)m << 5) | ((uint32_t)s2 << 8) | slotbits;
+                    const unsigned pmask = __ballot_sync(FULL, push);
+                    if (push) {
+                        const int w = (top + __popc(pmask & lt)) & (S - 1);
+                        sb[w] = child;
+                        sm[w] = cm;
+                    }
+                    top += __popc(pmask);
+                }
+                __syncwarp();
+
+                if (((++rounds) & 31) == 0 && rounds >= a.tune.min_rounds) {
+                    int ex = 0;
+                    if (lane == 0)
+                        ex = *(volatile int *)&a.ctrl->exited;
+                    ex = __shfl_sync(FULL, ex, 0);
+                    if (ex >= a.tune.exit_threshold) {
+                        stop = true;
+                        break;
+                    }
+                }
+            }
+            // flush this run's counters
+            fmin = warp_min_int(fmin);
+            if (lane == 0) {
+                atomicAdd(&a.cnt.search_nodes[inst0], nodes);
+                atomicAdd(&a.ctrl->search_nodes_total, nodes);
+                if (fmin != INT_MAX)
+                    atomicMin(&a.cnt.fnext_off[inst0], fmin);
+            }
+            if (stop) {
+                hand_back_stack<W, S>(a, sb, sm, bot, top - bot, inst0, my_origin, lane);
+                hand_back_records<W>(a, i + cnt, end, lane);
+                break;
+            }
+            i += cnt;
+        }
+        if (stop)
+            break;
+    }
+    if (!stop && lane == 0)
+        atomicAdd(&a.ctrl->exited, 1);
+}
+
+// ---------------------------------------------------------------------
+// Splitter: one block per problem; breadth-first, order-preserving
+// expansion of the problem's root until the level holds `target` records.
+// ---------------------------------------------------------------------
+template <int W> struct SplitArgs {
+    const unsigned *active;
+    InstState<W> *state;
+    Rec<W> *scratch;     // per problem: 2 * C records
+    int C;
+    int *count;          // records in the problem's final level
+    Counters cnt;
+    MoveLut<W> lut;
+};
+
+template <int W>
+__global__ void k_split(const SplitArgs<W> a)
+{
+    typedef typename Geo<W>::B B;
+    constexpr int BITS = Geo<W>::BITS;
+    __shared__ __align__(16) unsigned char lut[SharedLut<W>::BYTES];
+    __shared__ int warp_sums[32];
+    __shared__ int s_fmin, s_leaves_only;
+    __shared__ unsigned long long s_internal;
+    SharedLut<W>::load(lut, a.lut);
+
+    const int k = blockIdx.x;
+    const unsigned inst = a.active[k];
+    const InstState<W> st = a.state[inst];
+    Rec<W> *A = a.scratch + (size_t)k * 2 * a.C;
+    Rec<W> *Bf = A + a.C;
+    const B GOAL = goal_board<W>();
+    if (threadIdx.x == 0) {
+        Rec<W> r;
+        r.b = st.root;
+        r.meta = st.root_meta & M_NODE_MASK;
+        if (r.b == GOAL)
+            r.meta |= M_LEAF;
+        r.inst = inst;
+        r.origin = 0;
+        r.pm = 0;
+        A[0] = r;
+        s_fmin = INT_MAX;
+        s_internal = 0;
+        a.cnt.search_nodes[inst] = 0;
+        a.cnt.goals[inst] = 0;
+        a.cnt.goal_origin[inst] = 0xffffffffu;
+    }
+    __syncthreads();
+
+    const int T = max(1, (int)st.target);
+    int cnt = 1, depth = 0;
+    Rec<W> *cur = A, *nxt = Bf;
+    for (;;) {
+        if (cnt >= T || depth >= 16 || 4 * cnt > a.C)
+            break;
+        // stop once every node of the level is a goal leaf
+        if (threadIdx.x == 0)
+            s_leaves_only = 1;
+        __syncthreads();
+        for (int j = threadIdx.x; j < cnt; j += blockDim.x)
+            if (!(cur[j].meta & M_LEAF))
+                s_leaves_only = 0;
+        __syncthreads();
+        if (s_leaves_only)
+            break;
+
+        int outbase = 0;
+        int fmin = INT_MAX;
+        unsigned long long internal = 0;
+        for (int base = 0; base < cnt; base += blockDim.x) {
+            const int j = base + threadIdx.x;
+            Rec<W> r;
+            r.meta = M_LEAF;
+            const bool v = j < cnt;
+            if (v)
+                r = cur[j];
+            const bool leaf = v && (r.meta & M_LEAF);
+            const bool exp = v && !leaf;
+            Rec<W> c[4];
+            int nc = 0;
+            if (leaf) {
+                c[0] = r;
+                nc = 1;
+            } else if (exp) {
+                internal += 1;
+                const int p = (int)m_blank(r.meta);
+                const int last = (int)m_last(r.meta);
+                const int s = m_slack(r.meta);
+                const uint32_t d = m_hi(r.meta);
+                const LutRow<W> e = SharedLut<W>::row(lut, p);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    if (!e.legal(m) || last == 3 - m)
+                        continue;
+                    const int np = p + move_off<W>(m);
+                    const unsigned t = tile_at<W>(r.b, np);
+                    const int s2 = e.away(m, t) ? s - 2 : s;
+                    if (s2 < 0) {
+                        fmin = min(fmin, -s2);
+                        continue;
+                    }
+                    const B x = (B)t;
+                    Rec<W> ch;
+                    ch.b = r.b + (x << (BITS * p)) - (x << (BITS * np));
+                    ch.meta = (uint32_t)np | ((uint32_t)m << 5) | ((uint32_t)s2 << 8) | ((d + 1u) << 16);
+                    if (ch.b == GOAL)
+                        ch.meta |= M_LEAF;
+                    ch.inst = inst;
+                    ch.origin = 0;
+                    ch.pm = r.pm | ((uint32_t)m << (2 * d));
+                    c[nc++] = ch;
+                }
+            }
+            int total;
+            const int pos = block_exclusive_scan(nc, warp_sums, &total);
+            for (int q = 0; q < nc; ++q)
+                nxt[outbase + pos + q] = c[q];
+            outbase += total;
+        }
+        // block reductions of the level's counters
+        fmin = warp_min_int(fmin);
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&s_fmin, fmin);
+        }
+        for (int d2 = 16; d2; d2 >>= 1)
+            internal += __shfl_xor_sync(FULL, internal, d2);
+        if ((threadIdx.x & 31) == 0)
+            atomicAdd(&s_internal, internal);
+        __syncthreads();
+        Rec<W> *t = cur;
+        cur = nxt;
+        nxt = t;
+        cnt = outbase;
+        ++depth;
+    }
+    if (cur != A) {
+        for (int j = threadIdx.x; j < cnt; j += blockDim.x)
+            A[j] = cur[j];
+    }
+    if (threadIdx.x == 0) {
+        a.count[k] = cnt;
+        a.cnt.split_nodes[inst] = s_internal;
+        a.cnt.fnext_off[inst] = s_fmin;
+    }
+}
+
+// Exclusive scan of the per-problem record counts (one block).
+__global__ void k_scan(const int *count, int *offset, Ctrl *ctrl)
+{
+    __shared__ int warp_sums[32];
+    __shared__ int carry;
+    const int n = ctrl->n_active;
+    if (threadIdx.x == 0)
+        carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int j = base + threadIdx.x;
+        const int v = j < n ? count[j] : 0;
+        int total;
+        const int pos = block_exclusive_scan(v, warp_sums, &total);
+        if (j < n)
+            offset[j] = carry + pos;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        ctrl->n_in = carry;
+        ctrl->head = 0;
+        ctrl->out_count = 0;
+        ctrl->exited = 0;
+        ctrl->records_total += (unsigned long long)carry;
+    }
+}
+
+// Gather every problem's frontier into the first pass's queue; a record's
+// origin is its position in that queue.
+template <int W>
+__global__ void k_compact(const Rec<W> *scratch, int C, const int *count, const int *offset,
+                          Rec<W> *q)
+{
+    const int k = blockIdx.x;
+    const Rec<W> *A = scratch + (size_t)k * 2 * C;
+    const int n = count[k], o = offset[k];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        Rec<W> r = A[j];
+        r.origin = (uint32_t)(o + j);
+        q[o + j] = r;
+    }
+}
+
+// Between passes: the records handed back become the next input.
+__global__ void k_next_pass(Ctrl *ctrl)
+{
+    ctrl->max_out = max(ctrl->max_out, ctrl->out_count);
+    ctrl->n_in = ctrl->out_count;
+    ctrl->handed_back_total += (unsigned long long)ctrl->out_count;
+    ctrl->head = 0;
+    ctrl->out_count = 0;
+    ctrl->exited = 0;
+}
+
+// ---------------------------------------------------------------------
+// Advance: per problem, close the iteration (Algorithm 1's driver).
+// ---------------------------------------------------------------------
+template <int W> struct AdvanceArgs {
+    const unsigned *active;
+    unsigned *next_active;
+    InstState<W> *state;
+    const Rec<W> *scratch;
+    int C;
+    const int *count;
+    const int *offset;
+    Counters cnt;
+    Ctrl *ctrl;
+    Tune tune;
+    unsigned long long node_budget;
+    uint8_t *out_moves;
+    unsigned long long *out_nodes;
+};
+
+template <int W>
+__device__ bool take_goal_record(const AdvanceArgs<W> &a, int k, unsigned inst, InstState<W> &st)
+{
+    const unsigned go = a.cnt.goal_origin[inst];
+    const int local = (int)go - a.offset[k];
+    if (go == 0xffffffffu || local < 0 || local >= a.count[k])
+        return false;
+    const Rec<W> r = a.scratch[(size_t)k * 2 * a.C + local];
+    const int d = (int)m_hi(r.meta);
+    // every step must descend, and a goal can only sit at depth == limit
+    if (st.path_len + d > st.limit || (st.mode == MODE_PATH && d == 0))
+        return false;
+    if (r.b == goal_board<W>() && st.path_len + d != st.limit)
+        return false;
+    for (int j = 0; j < d; ++j)
+        a.out_moves[(size_t)inst * Geo<W>::MAXLEN + st.path_len + j] = (uint8_t)((r.pm >> (2 * j)) & 3u);
+    st.path_len += d;
+    if (st.path_len == st.limit) {
+        if (r.b != goal_board<W>())
+            return false;
+        st.mode = MODE_DONE;
+        st.status = 0;
+    } else {
+        st.mode = MODE_PATH;
+        st.root = r.b;
+        st.root_meta = r.meta & M_NODE_MASK;
+        st.target = (uint32_t)max(2, a.tune.target_path);
+    }
+    return true;
+}
+
+template <int W>
+__global__ void k_advance(const AdvanceArgs<W> a)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.ctrl->n_active)
+        return;
+    const unsigned inst = a.active[k];
+    InstState<W> st = a.state[inst];
+    const unsigned long long total = a.cnt.split_nodes[inst] + a.cnt.search_nodes[inst];
+    const unsigned long long goals = a.cnt.goals[inst];
+    if (st.mode == MODE_COUNT) {
+        a.out_nodes[(size_t)inst * Geo<W>::MAXIT + st.it] = total;
+        st.rows = st.it + 1;
+        st.cum_nodes += total;
+        if (goals > 0) {
+            st.length = st.limit;
+            st.solutions = goals;
+            if (!take_goal_record<W>(a, k, inst, st)) {
+                st.mode = MODE_DONE;
+                st.status = 8;  // BPIDA_EINTERNAL
+                atomicOr(&a.ctrl->err, ERR_INTERNAL);
+            }
+        } else {
+            const int off = a.cnt.fnext_off[inst];
+            if (off == INT_MAX || off <= 0) {
+                st.mode = MODE_DONE;
+                st.status = 8;
+                atomicOr(&a.ctrl->err, ERR_INTERNAL);
+            } else if (a.node_budget && st.cum_nodes > a.node_budget) {
+                st.mode = MODE_DONE;
+                st.status = 4;  // BPIDA_EBUDGET
+            } else if (st.it + 1 >= Geo<W>::MAXIT || st.limit + off > Geo<W>::MAXLEN) {
+                st.mode = MODE_DONE;
+                st.status = 7;  // BPIDA_ELIMIT
+            } else {
+                st.limit += off;
+                st.it += 1;
+                st.root = st.start;
+                st.root_meta = m_make(m_blank(st.start_meta), LAST_NONE, (uint32_t)(st.limit - st.h0));
+                unsigned long long want =
+                    (total * (unsigned long long)a.tune.growth) / (unsigned long long)a.tune.nodes_per_record;
+                want = want < 1ull ? 1ull : want;
+                want = want > (unsigned long long)a.tune.target_cap ? (unsigned long long)a.tune.target_cap : want;
+                st.target = (uint32_t)want;
+            }
+        }
+    } else if (st.mode == MODE_PATH) {
+        if (goals == 0 || !take_goal_record<W>(a, k, inst, st)) {
+            st.mode = MODE_DONE;
+            st.status = 8;
+            atomicOr(&a.ctrl->err, ERR_INTERNAL);
+        }
+    }
+    a.state[inst] = st;
+    if (st.mode != MODE_DONE) {
+        const int j = atomicAdd(&a.ctrl->n_next, 1);
+        a.next_active[j] = inst;
+    }
+}
+
+__global__ void k_step_end(Ctrl *ctrl)
+{
+    ctrl->n_active = ctrl->n_next;
+    ctrl->n_next = 0;
+}
+
+// ---------------------------------------------------------------------
+// Init / finalize
+// ---------------------------------------------------------------------
+template <int W> struct InitArgs {
+    const uint64_t *boards;
+    int n;
+    InstState<W> *state;
+    unsigned *active;
+    Ctrl *ctrl;
+    uint8_t *out_moves;
+    unsigned long long *out_nodes;
+};
+
+template <int W>
+__global__ void k_init(const InitArgs<W> a)
+{
+    typedef typename Geo<W>::B B;
+    constexpr int N = Geo<W>::N, BITS = Geo<W>::BITS;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n)
+        return;
+    for (int j = 0; j < Geo<W>::MAXLEN; ++j)
+        a.out_moves[(size_t)i * Geo<W>::MAXLEN + j] = 0;
+    for (int j = 0; j < Geo<W>::MAXIT; ++j)
+        a.out_nodes[(size_t)i * Geo<W>::MAXIT + j] = 0ull;
+    B b;
+    if constexpr (W <= 4) {
+        b = (B)a.boards[i];
+    } else {
+        b = (B)a.boards[2 * (size_t)i] | ((B)a.boards[2 * (size_t)i + 1] << 64);
+    }
+    InstState<W> st;
+    st.start = b;
+    st.root = b;
+    st.it = 0;
+    st.rows = 0;
+    st.path_len = 0;
+    st.length = -1;
+    st.cum_nodes = 0;
+    st.solutions = 0;
+    st.target = 1;
+    st.pad = 0;
+    // permutation check, blank, Manhattan distance, parity class
+    uint32_t seen = 0;
+    int blank = -1, h = 0, inv = 0;
+    bool ok = true;
+    unsigned tiles[N];
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+        const unsigned t = tile_at<W>(b, p);
+        tiles[p] = t;
+        if (t >= (unsigned)N || (seen >> t) & 1u)
+            ok = false;
+        else
+            seen |= 1u << t;
+        if (t == 0)
+            blank = p;
+        else
+            h += abs(p / W - (int)t / W) + abs(p % W - (int)t % W);
+    }
+    if constexpr (W != 4) {
+        // bits above the last position must be clear
+        if ((b >> (BITS * N)) != 0)
+            ok = false;
+    }
+    if (ok) {
+        for (int x = 0; x < N; ++x)
+            for (int y = x + 1; y < N; ++y)
+                if (tiles[x] && tiles[y] && tiles[x] > tiles[y])
+                    ++inv;
+        const int parity = (W & 1) ? (inv & 1) : ((inv + blank / W) & 1);
+        ok = parity == 0;
+    }
+    if (!ok) {
+        st.start_meta = 0;
+        st.root_meta = 0;
+        st.h0 = -1;
+        st.limit = -1;
+        st.mode = MODE_DONE;
+        st.status = 1;  // BPIDA_EINVAL
+        a.state[i] = st;
+        return;
+    }
+    if (h > Geo<W>::MAXLEN) {
+        st.start_meta = 0;
+        st.root_meta = 0;
+        st.h0 = h;
+        st.limit = h;
+        st.mode = MODE_DONE;
+        st.status = 7;  // BPIDA_ELIMIT
+        a.state[i] = st;
+        return;
+    }
+    st.h0 = h;
+    st.limit = h;
+    st.start_meta = m_make((uint32_t)blank, LAST_NONE, 0);
+    st.root_meta = st.start_meta;
+    st.mode = MODE_COUNT;
+    st.status = 0;
+    a.state[i] = st;
+    const int j = atomicAdd(&a.ctrl->n_active, 1);
+    a.active[j] = (unsigned)i;
+}
+
+template <int W>
+__global__ void k_finalize(const InstState<W> *state, int n, int *out_len, int *out_iters,
+                           int *out_status, int abort_status)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const InstState<W> st = state[i];
+    const bool solved = st.mode == MODE_DONE && st.status == 0;
+    out_len[i] = solved ? st.length : -1;
+    if (out_iters)
+        out_iters[i] = st.rows;
+    if (out_status)
+        out_status[i] = st.mode == MODE_DONE ? st.status : (abort_status ? abort_status : 8);
+}
+
+}  // namespace bp

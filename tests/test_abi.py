@@ -1,0 +1,47 @@
+"""The C ABI library builds, loads and exports every function that
+include/bpida.h declares (no compute calls: no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1705_02843_gb300 import bpida
+from paper_1705_02843_gb300 import build as pkg_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "bpida.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bpida_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pkg_build.build()
+    return ctypes.CDLL(bpida.LIB_PATH)
+
+
+def test_header_declares_the_expected_calls():
+    names = declared_functions()
+    assert "bpida_solve" in names and "bpida_solve_ex" in names
+    assert set(names) == set(bpida.EXPORTS)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_host_only_calls(lib):
+    b = bpida.load()
+    assert b.bpida_max_len(4) == 80 and b.bpida_max_iters(4) == 41
+    assert b.bpida_max_len(3) >= 31 and b.bpida_max_len(5) >= 100
+    assert b.bpida_max_len(7) == 0
+    assert bpida.status_str(bpida.EBUDGET) == "node budget exhausted"
+
+
+def test_config_struct_layout():
+    assert ctypes.sizeof(bpida.Config) == 7 * 4 + 4 + 8

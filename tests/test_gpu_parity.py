@@ -1,0 +1,162 @@
+"""CUDA path vs the CPU oracle, bit-exact on every integer result.
+
+Every test calls the C ABI (libbpida.so) through the Python binding on
+seeded synthetic boards and compares, per instance: status, optimal length,
+nodes expanded in every iteration (all-solutions mode, so the final
+iteration's count is order-free) and the first solution, which must be the
+oracle's (the lexicographically first optimal move sequence in U<L<R<D
+order) and must replay to the goal.
+"""
+import json
+import os
+import random
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1705_02843_gb300 import bpida
+from paper_1705_02843_gb300 import inputs as I
+from tests import puzzle_ref as P
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def gpu_solve(W, boards_tiles, **cfg):
+    packed = [I.pack(W, t) for t in boards_tiles]
+    arr = np.array(packed, dtype=np.uint64).reshape(-1) if W <= 4 else np.array(packed, dtype=np.uint64).reshape(-1, 2)
+    t = torch.from_numpy(arr.view(np.int64)).to("cuda:0")
+    sol = bpida.solve(t, W, bpida.make_config(W, **cfg))
+    torch.cuda.synchronize()
+    return sol.status, sol.to_host()
+
+
+def check_against(W, tiles, got, ref):
+    assert len(got) == len(ref)
+    for i, (g, r) in enumerate(zip(got, ref)):
+        assert g["status"] == r.status, (i, g["status"], r.status)
+        if r.status != oracle.OK:
+            continue
+        assert g["length"] == r.length, (i, g["length"], r.length)
+        assert g["nodes"] == r.nodes, (i, g["nodes"], r.nodes)
+        assert g["iters"] == r.iters
+        assert g["moves"] == r.moves, (i, g["moves"], r.moves)
+        assert P.replay(W, tiles[i], g["moves"]) == list(range(W * W))
+
+
+def test_walks15_16x40():
+    insts = I.walks15_16x40()
+    tiles = [x.tiles for x in insts]
+    rc, got = gpu_solve(4, tiles)
+    assert rc == bpida.OK
+    check_against(4, tiles, got, oracle.solve_batch(4, np.array(tiles, dtype=np.uint8)))
+
+
+def test_edge_cases_15():
+    goal = list(range(16))
+    one = [1, 0] + list(range(2, 16))
+    two = [1, 2, 0] + list(range(3, 16))
+    walk = I.walks15_16x40()[3].tiles
+    unsolvable = list(walk)
+    a, b = [p for p in range(16) if unsolvable[p]][:2]
+    unsolvable[a], unsolvable[b] = unsolvable[b], unsolvable[a]
+    notperm = [1] * 16
+    tiles = [goal, one, unsolvable, two, notperm, walk]
+    rc, got = gpu_solve(4, tiles)
+    assert rc == bpida.OK
+    assert got[0]["length"] == 0 and got[0]["nodes"] == [1] and got[0]["moves"] == []
+    assert got[1]["length"] == 1 and got[1]["nodes"] == [2] and got[1]["moves"] == [1]
+    assert got[3]["length"] == 2 and got[3]["nodes"] == [3] and got[3]["moves"] == [1, 1]
+    for i in (2, 4):
+        assert got[i]["status"] == bpida.EINVAL and got[i]["length"] == -1
+    ref = oracle.solve_batch(4, np.array([t if i not in (4,) else goal for i, t in enumerate(tiles)], dtype=np.uint8))
+    for i in (0, 1, 3, 5):
+        assert got[i]["nodes"] == ref[i].nodes and got[i]["moves"] == ref[i].moves
+
+
+def test_empty_batch():
+    t = torch.zeros(0, dtype=torch.int64, device="cuda:0")
+    sol = bpida.solve(t, 4)
+    assert sol.status == bpida.OK and sol.length.numel() == 0
+
+
+@pytest.mark.parametrize("n", [1, 33, 257])
+def test_ragged_batches(n):
+    rng = random.Random(n)
+    insts = [I.make_walk(4, 7000 + i, rng.randint(0, 36)) for i in range(n)]
+    tiles = [x.tiles for x in insts]
+    rc, got = gpu_solve(4, tiles)
+    assert rc == bpida.OK
+    check_against(4, tiles, got, oracle.solve_batch(4, np.array(tiles, dtype=np.uint8)))
+
+
+def test_all_8puzzle_states():
+    dist, count, order = P.bfs8()
+    tiles = [list(s) for s in order]
+    rc, got = gpu_solve(3, tiles)
+    assert rc == bpida.OK
+    ref = oracle.solve_batch(3, np.array(tiles, dtype=np.uint8))
+    for i, (s, g, r) in enumerate(zip(order, got, ref)):
+        assert g["length"] == dist[s]
+        assert g["nodes"] == r.nodes, (i, g["nodes"], r.nodes)
+        assert g["moves"] == r.moves
+    rs = random.Random(1)
+    for i in rs.sample(range(len(order)), 2000):
+        assert P.replay(3, tiles[i], got[i]["moves"]) == list(range(9))
+
+
+@pytest.mark.parametrize("cfg", [
+    dict(stack_entries=256), dict(stack_entries=1024), dict(warps_per_block=8),
+    dict(split_target=1), dict(split_target=2, min_rounds=32, exit_fraction_pct=1),
+    dict(split_target=64, exit_fraction_pct=90),
+])
+def test_tuning_knobs_do_not_change_results(cfg):
+    insts = I.walks15_16x40()[:8]
+    tiles = [x.tiles for x in insts]
+    rc, got = gpu_solve(4, tiles, **cfg)
+    assert rc == bpida.OK
+    check_against(4, tiles, got, oracle.solve_batch(4, np.array(tiles, dtype=np.uint8)))
+
+
+def test_node_budget():
+    insts = I.walks15_16x40()[:2]
+    tiles = [x.tiles for x in insts]
+    rc, got = gpu_solve(4, tiles, node_budget=50)
+    assert all(g["status"] == bpida.EBUDGET and g["length"] == -1 for g in got)
+    ref = oracle.solve_batch(4, np.array(tiles, dtype=np.uint8))
+    for g, r in zip(got, ref):
+        # completed iterations before the budget ran out are exact
+        assert g["nodes"] == r.nodes[:len(g["nodes"])]
+
+
+def test_24puzzle_walks():
+    insts = [I.make_walk(5, 900 + s, 30 + 2 * s) for s in range(12)]
+    tiles = [x.tiles for x in insts]
+    rc, got = gpu_solve(5, tiles)
+    assert rc == bpida.OK
+    check_against(5, tiles, got, oracle.solve_batch(5, np.array(tiles, dtype=np.uint8)))
+
+
+def _golden(name):
+    path = os.path.join(GOLDEN, name + ".json")
+    if not os.path.exists(path):
+        pytest.skip("no stored oracle results for " + name)
+    with open(path) as f:
+        return json.load(f)
+
+
+def test_perms15_100_sampled_cheap():
+    """Random permutations whose oracle results are stored, cheapest first."""
+    doc = _golden("perms15_100")
+    insts = I.perms15_100()
+    recs = sorted((r for r in doc["instances"] if r["status"] == 0), key=lambda r: sum(r["nodes"]))[:40]
+    tiles = [insts[r["index"]].tiles for r in recs]
+    rc, got = gpu_solve(4, tiles)
+    assert rc == bpida.OK
+    for r, g, t in zip(recs, got, tiles):
+        assert g["length"] == r["length"]
+        assert g["nodes"] == r["nodes"]
+        assert "".join(map(str, g["moves"])) == r["moves"]
+        assert P.replay(4, t, g["moves"]) == list(range(16))
