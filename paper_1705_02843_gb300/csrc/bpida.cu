@@ -138,7 +138,7 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
 
     const int wpb = cfg.wpb;
     const int threads = wpb * 32;
-    const size_t smem = SharedLut<W>::BYTES + (size_t)wpb * S * (sizeof(B) + sizeof(uint32_t));
+    const size_t smem = SharedLut<W>::BYTES + (size_t)wpb * S * WarpStack<W>::ENTRY_BYTES;
     CK(cudaFuncSetAttribute(k_search<W, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int bpsm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_search<W, S>, threads, smem));

@@ -25,6 +25,7 @@
 #include <stdint.h>
 #include <limits.h>
 #include <cuda_runtime.h>
+#include <type_traits>
 
 namespace bp {
 
@@ -271,10 +272,117 @@ template <int W> struct SearchArgs {
     MoveLut<W> lut;
 };
 
+// ---- warp stack entries ----
+// Stack metadata (32 bits), different from the record metadata:
+//  bits 0..4  blank position
+//  bits 5..8  excluded move mask (the inverse of the move that made the
+//             node; 0 for an instance root)
+//  bits 9..16 slack = limit - g - h
+__device__ __forceinline__ uint32_t sm_from_rec(uint32_t m)
+{
+    const uint32_t last = m_last(m);
+    const uint32_t excl = last < 4u ? (1u << (3u - last)) : 0u;
+    return m_blank(m) | (excl << 5) | ((uint32_t)m_slack(m) << 9);
+}
+__device__ __forceinline__ uint32_t rec_from_sm(uint32_t m)
+{
+    const uint32_t excl = (m >> 5) & 15u;
+    const uint32_t last = excl ? 3u - (uint32_t)(__ffs(excl) - 1) : LAST_NONE;
+    return m_make(m & 31u, last, (m >> 9) & 255u);
+}
+
+// W <= 4: one 16-byte entry {board lo, board hi, meta, origin}.
+// W == 5: a 16-byte board array and an 8-byte {meta, origin} array.
+template <int W, bool Wide = (W == 5)> struct WarpStack;
+template <int W> struct WarpStack<W, false> {
+    static constexpr int ENTRY_BYTES = 16;
+    uint4 *e;
+    __device__ __forceinline__ void init(unsigned char *base, int) { e = (uint4 *)base; }
+    __device__ __forceinline__ void put(int i, uint64_t b, uint32_t meta, uint32_t org)
+    {
+        e[i] = make_uint4((uint32_t)b, (uint32_t)(b >> 32), meta, org);
+    }
+    __device__ __forceinline__ void get(int i, uint64_t &b, uint32_t &meta, uint32_t &org) const
+    {
+        const uint4 v = e[i];
+        b = ((uint64_t)v.y << 32) | v.x;
+        meta = v.z;
+        org = v.w;
+    }
+};
+template <int W> struct WarpStack<W, true> {
+    static constexpr int ENTRY_BYTES = 24;
+    uint4 *eb;
+    uint2 *em;
+    __device__ __forceinline__ void init(unsigned char *base, int S)
+    {
+        eb = (uint4 *)base;
+        em = (uint2 *)(eb + S);
+    }
+    __device__ __forceinline__ void put(int i, u128 b, uint32_t meta, uint32_t org)
+    {
+        eb[i] = make_uint4((uint32_t)b, (uint32_t)(b >> 32), (uint32_t)(b >> 64), (uint32_t)(b >> 96));
+        em[i] = make_uint2(meta, org);
+    }
+    __device__ __forceinline__ void get(int i, u128 &b, uint32_t &meta, uint32_t &org) const
+    {
+        const uint4 v = eb[i];
+        b = ((u128)v.w << 96) | ((u128)v.z << 64) | ((u128)v.y << 32) | v.x;
+        const uint2 m = em[i];
+        meta = m.x;
+        org = m.y;
+    }
+};
+
+// Legal blank moves of every position, 4 bits per position (bit m = move m
+// keeps the blank on the board), as one integer constant.
+template <int W> struct LegalMoves {
+    typedef typename std::conditional<(W <= 4), uint64_t, u128>::type T;
+    __host__ __device__ static constexpr T make()
+    {
+        T v = 0;
+        for (int p = 0; p < W * W; ++p) {
+            const int r = p / W, c = p % W;
+            const unsigned m = (r > 0 ? 1u : 0u) | (c > 0 ? 2u : 0u) | (c < W - 1 ? 4u : 0u) | (r < W - 1 ? 8u : 0u);
+            v |= (T)m << (4 * p);
+        }
+        return v;
+    }
+    __device__ static __forceinline__ unsigned at(int p)
+    {
+        constexpr T V = make();
+        return (unsigned)(V >> (4 * p)) & 15u;
+    }
+};
+
+// Move tables for the XOR child update: sliding tile t between positions
+// q = min(p, np) and q + |off| flips t in both fields, i.e.
+// child = board ^ ((t * (1 + 2^(BITS*|off|))) << (BITS*q)).
+template <int W> __device__ __forceinline__ unsigned move_mul(int m)
+{
+    constexpr int BITS = Geo<W>::BITS;
+    return (m == 0 || m == 3) ? (1u + (1u << (BITS * W))) : (1u + (1u << BITS));
+}
+template <int W> __device__ __forceinline__ int move_low(int m)
+{
+    return m == 0 ? -W : m == 1 ? -1 : 0;  // min(0, off)
+}
+
+// away bit of the Manhattan table row for move m and tile t
+template <int W> __device__ __forceinline__ bool away_bit(const LutRow<W> &row, int m, unsigned t)
+{
+    if constexpr (W <= 4) {
+        const uint32_t lo = (uint32_t)row.v, hi = (uint32_t)(row.v >> 32);
+        const uint32_t w = (m < 2) ? lo : hi;
+        return (w >> (((m & 1) << 4) + t)) & 1u;
+    } else {
+        return (row.w(m) >> t) & 1u;
+    }
+}
+
 template <int W, int S>
-__device__ __forceinline__ void hand_back_stack(const SearchArgs<W> &a, typename Geo<W>::B *sb,
-                                                uint32_t *sm, int from, int k, unsigned inst,
-                                                unsigned my_origin, int lane)
+__device__ __forceinline__ void hand_back_stack(const SearchArgs<W> &a, const WarpStack<W> &stk, int from,
+                                                int k, unsigned inst, int lane)
 {
     if (k <= 0)
         return;
@@ -282,26 +390,22 @@ __device__ __forceinline__ void hand_back_stack(const SearchArgs<W> &a, typename
     if (lane == 0)
         base = atomicAdd(&a.ctrl->out_count, k);
     base = __shfl_sync(FULL, base, 0);
-    const bool fits = base + k <= a.out_cap;
-    if (!fits) {
+    if (base + k > a.out_cap) {
         if (lane == 0)
             atomicOr(&a.ctrl->err, ERR_QUEUE);
+        return;
     }
-    for (int j0 = 0; j0 < k; j0 += 32) {
-        const int j = j0 + lane;
-        const bool ok = j < k;
-        const int si = (from + j) & (S - 1);
-        uint32_t m = ok ? sm[si] : 0u;
-        unsigned o = __shfl_sync(FULL, my_origin, m_hi(m));
-        if (ok && fits) {
-            Rec<W> r;
-            r.b = sb[si];
-            r.meta = m & M_NODE_MASK;
-            r.inst = inst;
-            r.origin = o;
-            r.pm = 0;
-            a.out[base + j] = r;
-        }
+    for (int j = lane; j < k; j += 32) {
+        typename Geo<W>::B b;
+        uint32_t m, o;
+        stk.get((from + j) & (S - 1), b, m, o);
+        Rec<W> r;
+        r.b = b;
+        r.meta = rec_from_sm(m);
+        r.inst = inst;
+        r.origin = o;
+        r.pm = 0;
+        a.out[base + j] = r;
     }
 }
 
@@ -324,6 +428,13 @@ __device__ __forceinline__ void hand_back_records(const SearchArgs<W> &a, int fr
         a.out[base + j] = a.in[from + j];
 }
 
+// One warp = one shared stack (Algorithm 1's openList). Each round pops up
+// to 32 nodes (one per lane), tests them for the goal, and generates the
+// children of the rest; children with f <= limit are pushed at slots
+// reserved by ballot/popc (a linearizable put with one writer per slot),
+// the others only contribute f_next. The warp takes runs of same-instance
+// records from the pass's input queue until it is exhausted; once enough
+// warps have run dry, busy warps hand their open nodes to the next pass.
 template <int W, int S>
 __global__ void k_search(const SearchArgs<W> a)
 {
@@ -335,9 +446,8 @@ __global__ void k_search(const SearchArgs<W> a)
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    B *sb = (B *)(smem + SharedLut<W>::BYTES) + (size_t)warp * S;
-    uint32_t *sm = (uint32_t *)((B *)(smem + SharedLut<W>::BYTES) + (size_t)(blockDim.x >> 5) * S) +
-                   (size_t)warp * S;
+    WarpStack<W> stk;
+    stk.init(smem + SharedLut<W>::BYTES + (size_t)warp * S * WarpStack<W>::ENTRY_BYTES, S);
     const unsigned lt = (1u << lane) - 1u;
     const B GOAL = goal_board<W>();
     const int n_in = a.ctrl->n_in;
@@ -356,7 +466,7 @@ __global__ void k_search(const SearchArgs<W> a)
         const int end = min(h + chunk, n_in);
         int i = h;
         while (i < end) {
-            // take the run of records [i, i+cnt) that belong to one instance
+            // the run of records [i, i+cnt) that belong to one instance
             const int idx = i + lane;
             const bool v = idx < end;
             Rec<W> r;
@@ -366,11 +476,8 @@ __global__ void k_search(const SearchArgs<W> a)
             const unsigned inst0 = __shfl_sync(FULL, inst, 0);
             const unsigned same = __ballot_sync(FULL, v && inst == inst0);
             const int cnt = (same == FULL) ? 32 : (__ffs(~same) - 1);
-            const unsigned my_origin = v ? r.origin : 0u;
-            if (lane < cnt) {
-                sb[lane] = r.b;
-                sm[lane] = (r.meta & M_NODE_MASK) | ((uint32_t)lane << 16);
-            }
+            if (lane < cnt)
+                stk.put(lane, r.b, sm_from_rec(r.meta), r.origin);
             int top = cnt, bot = 0;
             __syncwarp();
             unsigned long long nodes = 0;
@@ -386,18 +493,15 @@ __global__ void k_search(const SearchArgs<W> a)
                     const int k = min(size - n, S / 2);
                     if (lane == 0)
                         atomicAdd(&a.ctrl->spills, 1ull);
-                    hand_back_stack<W, S>(a, sb, sm, bot, k, inst0, my_origin, lane);
+                    hand_back_stack<W, S>(a, stk, bot, k, inst0, lane);
                     bot += k;
                     __syncwarp();
                 }
                 const bool act = lane < n;
-                const int si = (top - n + lane) & (S - 1);
                 B b = 0;
-                uint32_t mt = 0;
-                if (act) {
-                    b = sb[si];
-                    mt = sm[si];
-                }
+                uint32_t mt = 0, org = 0;
+                if (act)
+                    stk.get((top - n + lane) & (S - 1), b, mt, org);
                 top -= n;
                 nodes += (unsigned long long)n;
                 __syncwarp();
@@ -405,41 +509,41 @@ __global__ void k_search(const SearchArgs<W> a)
                 const bool goal = act && (b == GOAL);
                 const unsigned gmask = __ballot_sync(FULL, goal);
                 if (gmask) {
-                    unsigned o = __shfl_sync(FULL, my_origin, m_hi(mt));
-                    o = warp_min_u32(goal ? o : 0xffffffffu);
+                    const unsigned o = warp_min_u32(goal ? org : 0xffffffffu);
                     if (lane == 0) {
                         atomicAdd(&a.cnt.goals[inst0], (unsigned long long)__popc(gmask));
                         atomicMin(&a.cnt.goal_origin[inst0], o);
                     }
                 }
-                const bool expand = act && !goal;
-                const int p = (int)m_blank(mt);
-                const int last = (int)m_last(mt);
-                const int s = m_slack(mt);
-                const uint32_t slotbits = mt & (31u << 16);
-                const LutRow<W> e = SharedLut<W>::row(lut, p);
+                const int p = (int)(mt & 31u);
+                const int s = (int)((mt >> 9) & 255u);
+                const unsigned allowed = (act && !goal) ? (LegalMoves<W>::at(p) & ~((mt >> 5) & 15u)) : 0u;
+                const bool low = s < 2;
+                const uint32_t sbase = (uint32_t)s << 9;
+                const LutRow<W> row = SharedLut<W>::row(lut, p);
+                bool pruned = false;
+                int base = top;
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
-                    const bool legal = expand && e.legal(m) && (last != 3 - m);
+                    const bool legal = (allowed >> m) & 1u;
                     const int np = legal ? p + move_off<W>(m) : p;
                     const unsigned t = tile_at<W>(b, np);
-                    // h changes by +1 (away from goal cell) or -1, g by +1:
-                    // the child's slack is s - 2 or s
-                    const int s2 = e.away(m, t) ? s - 2 : s;
-                    const bool push = legal && s2 >= 0;
-                    if (legal && s2 < 0)
-                        fmin = min(fmin, -s2);
-                    const B x = (B)t;
-                    const B child = b + (x << (BITS * p)) - (x << (BITS * np));
-                    const uint32_t cm = (uint32_t)np | ((uint32_t)m << 5) | ((uint32_t)s2 << 8) | slotbits;
-                    const unsigned pmask = __ballot_sync(FULL, push);
-                    if (push) {
-                        const int w = (top + __popc(pmask & lt)) & (S - 1);
-                        sb[w] = child;
-                        sm[w] = cm;
-                    }
-                    top += __popc(pmask);
+                    // h changes by +1 (away from the tile's goal cell) or -1
+                    // and g by +1, so the child's slack is s - 2 or s
+                    const bool away = away_bit<W>(row, m, t);
+                    const bool push = legal && !(away && low);
+                    pruned |= legal && away && low;
+                    const int q = legal ? p + move_low<W>(m) : 0;
+                    const B child = b ^ ((B)(t * move_mul<W>(m)) << (BITS * q));
+                    const uint32_t cm = ((uint32_t)np | ((1u << (3 - m)) << 5) | sbase) - (away ? (2u << 9) : 0u);
+                    const unsigned pm = __ballot_sync(FULL, push);
+                    if (push)
+                        stk.put((base + __popc(pm & lt)) & (S - 1), child, cm, org);
+                    base += __popc(pm);
                 }
+                top = base;
+                if (pruned)
+                    fmin = min(fmin, 2 - s);
                 __syncwarp();
 
                 if (((++rounds) & 31) == 0 && rounds >= a.tune.min_rounds) {
@@ -462,7 +566,7 @@ __global__ void k_search(const SearchArgs<W> a)
                     atomicMin(&a.cnt.fnext_off[inst0], fmin);
             }
             if (stop) {
-                hand_back_stack<W, S>(a, sb, sm, bot, top - bot, inst0, my_origin, lane);
+                hand_back_stack<W, S>(a, stk, bot, top - bot, inst0, lane);
                 hand_back_records<W>(a, i + cnt, end, lane);
                 break;
             }
