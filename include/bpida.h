@@ -29,10 +29,10 @@
  *
  * Streams and ownership: every pointer argument of the solve calls is
  * DEVICE memory owned by the caller; the library keeps no reference after
- * returning. Work is issued on `stream`; the call returns once the results
- * are written (the threshold loop reads small control words back to the
- * host). The library owns a per-device workspace that it grows on demand
- * and frees in bpida_release_workspace().
+ * returning. Work is issued on `stream` and the call returns once the
+ * results are written (it synchronises `stream` before returning). The
+ * library owns a per-device workspace that it grows on demand and frees in
+ * bpida_release_workspace(); calls are serialised by a process-wide lock.
  *
  * Errors: arguments the host can check are rejected synchronously with
  * BPIDA_EINVAL before any work is issued. Per-instance problems are
@@ -75,6 +75,12 @@ typedef struct {
     int min_rounds;       /* rounds a warp runs before it may hand back its
                              stack; 0 = auto */
     uint64_t node_budget; /* per instance, over all iterations; 0 = none */
+    int driver;           /* 0 = the threshold loop runs as one CUDA graph
+                             with device-set loop conditions (default);
+                             1 = the host launches every kernel and reads
+                             the loop state back after every search pass
+                             (needed for per-launch CUDA-event timing) */
+    int reserved;
 } bpida_config;
 
 typedef struct {
@@ -83,14 +89,18 @@ typedef struct {
     uint64_t records;       /* frontier records produced by the splitter */
     uint64_t handed_back;   /* stack entries handed back between passes */
     uint64_t search_nodes;  /* nodes expanded inside the search kernel */
-    double search_ms;       /* sum of search kernel durations (CUDA events
-                               on the launching stream); 0 unless timed */
+    double search_ms;       /* sum of search kernel durations from CUDA
+                               events on the launching stream; only with
+                               bpida_set_timing(1) and driver = 1 */
     int grid_blocks;        /* search kernel grid */
     int block_threads;      /* search kernel block */
     int sm_count;
     int launches;           /* kernels launched by the call */
     uint64_t spills;        /* stack overflows handed to the next pass */
     int max_handed_back;    /* largest hand-back queue of one pass */
+    double search_ms_device;/* sum of search kernel durations measured on
+                               the device (first block start to last block
+                               end, %globaltimer), any driver */
 } bpida_stats;
 
 /* Upper bounds used to size the per-instance output rows. */

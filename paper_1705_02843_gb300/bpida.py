@@ -34,6 +34,8 @@ class Config(ctypes.Structure):
         ("exit_fraction_pct", ctypes.c_int),
         ("min_rounds", ctypes.c_int),
         ("node_budget", ctypes.c_uint64),
+        ("driver", ctypes.c_int),
+        ("reserved", ctypes.c_int),
     ]
 
 
@@ -51,6 +53,7 @@ class Stats(ctypes.Structure):
         ("launches", ctypes.c_int),
         ("spills", ctypes.c_uint64),
         ("max_handed_back", ctypes.c_int),
+        ("search_ms_device", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -144,9 +147,9 @@ class Solution:
 
 def make_config(width: int = 4, split_target: int = 0, warps_per_block: int = 0,
                 stack_entries: int = 0, exit_fraction_pct: int = 0, min_rounds: int = 0,
-                node_budget: int = 0) -> Config:
+                node_budget: int = 0, driver: int = 0) -> Config:
     return Config(width, 1, split_target, warps_per_block, stack_entries, exit_fraction_pct,
-                  min_rounds, node_budget)
+                  min_rounds, node_budget, driver, 0)
 
 
 def solve(boards: torch.Tensor, width: int = 4, config: Optional[Config] = None,

@@ -5,10 +5,17 @@
 // f-limited iteration of every still-active instance (each at its own
 // limit): k_split builds each instance's root set, k_scan/k_compact gather
 // the root sets into one queue, k_search passes consume the queue with
-// persistent warps (further passes only when warps handed work back), and
+// persistent warps (another pass only when warps handed work back), and
 // k_advance records the iteration's node count and raises each limit to the
 // smallest pruned f (or, once a goal was popped, walks down the first
 // goal-bearing root to recover the solution path).
+//
+// By default the whole loop is one CUDA graph: the step loop and the pass
+// loop are conditional WHILE nodes whose conditions are set on the device
+// (k_step_end, k_pass_end), so a call is one graph launch and one final
+// synchronisation. The host-driven loop (driver = 1) launches the same
+// kernels one by one and reads the control block back after every pass; it
+// is what times each search launch with CUDA events.
 #include "bpida.h"
 #include "bpida_device.cuh"
 
@@ -16,7 +23,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 using namespace bp;
@@ -32,35 +41,59 @@ struct DevBuf {
     size_t n = 0;
 };
 
-cudaError_t ensure(DevBuf &b, size_t bytes)
-{
-    if (bytes == 0)
-        bytes = 16;
-    if (b.n >= bytes)
-        return cudaSuccess;
-    if (b.p)
-        cudaFree(b.p);
-    b.p = nullptr;
-    b.n = 0;
-    cudaError_t e = cudaMalloc(&b.p, bytes);
-    if (e == cudaSuccess)
-        b.n = bytes;
-    return e;
-}
+// W, S, warps per block, n, frontier cap, hand-back percentage, min rounds
+typedef std::tuple<int, int, int, int, int, int, int> PlanKey;
+
+struct Plan {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned gen = 0;  // workspace generation the graph was built for
+    void destroy()
+    {
+        if (exec)
+            cudaGraphExecDestroy(exec);
+        if (graph)
+            cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+    }
+};
 
 struct Workspace {
-    DevBuf state, act0, act1, ctr, scratch, count, offset, q0, q1, ctrl;
+    DevBuf state, act0, act1, ctr, scratch, count, offset, q0, q1, ctrl, desc;
     Ctrl *h_ctrl = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    unsigned gen = 1;  // bumped whenever a buffer moves
+    std::map<PlanKey, Plan> plans;
+
+    cudaError_t ensure(DevBuf &b, size_t bytes)
+    {
+        bytes = std::max<size_t>(bytes, 256);
+        if (b.n >= bytes)
+            return cudaSuccess;
+        if (b.p)
+            cudaFree(b.p);
+        b.p = nullptr;
+        b.n = 0;
+        ++gen;
+        cudaError_t e = cudaMalloc(&b.p, bytes);
+        if (e == cudaSuccess)
+            b.n = bytes;
+        return e;
+    }
     void release()
     {
-        DevBuf *all[] = {&state, &act0, &act1, &ctr, &scratch, &count, &offset, &q0, &q1, &ctrl};
+        for (auto &kv : plans)
+            kv.second.destroy();
+        plans.clear();
+        DevBuf *all[] = {&state, &act0, &act1, &ctr, &scratch, &count, &offset, &q0, &q1, &ctrl, &desc};
         for (DevBuf *b : all) {
             if (b->p)
                 cudaFree(b->p);
             b->p = nullptr;
             b->n = 0;
         }
+        ++gen;
         if (h_ctrl)
             cudaFreeHost(h_ctrl);
         h_ctrl = nullptr;
@@ -112,7 +145,7 @@ template <int W> MoveLut<W> make_lut()
 }
 
 struct Settings {
-    int width, count_all, split_target, wpb, S, exit_pct, min_rounds;
+    int width, count_all, split_target, wpb, S, exit_pct, min_rounds, driver;
     uint64_t budget;
 };
 
@@ -125,51 +158,141 @@ struct Settings {
         }                                                                                         \
     } while (0)
 
+// Adds a kernel node; the arguments are copied into the node.
+template <typename... P, typename... A>
+cudaError_t add_kernel(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode_t *dep, size_t ndep,
+                       void (*f)(P...), dim3 grid, dim3 block, size_t smem, A... args)
+{
+    void *ptrs[] = {(void *)&args...};
+    cudaKernelNodeParams kp;
+    std::memset(&kp, 0, sizeof kp);
+    kp.func = (void *)f;
+    kp.gridDim = grid;
+    kp.blockDim = block;
+    kp.sharedMemBytes = (unsigned)smem;
+    kp.kernelParams = ptrs;
+    return cudaGraphAddKernelNode(node, g, dep, ndep, &kp);
+}
+
+cudaError_t add_while(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode_t *dep, size_t ndep,
+                      cudaGraphConditionalHandle h, cudaGraph_t *body)
+{
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaError_t e = cudaGraphAddNode(node, g, dep, nullptr, ndep, &cp);
+    if (e == cudaSuccess)
+        *body = cp.conditional.phGraph_out[0];
+    return e;
+}
+
+struct Geometry {
+    int grid, threads, total_warps, C, tcap;
+    size_t smem, Q;
+    int n_cap;
+};
+
+// The whole solve as one graph:
+//   reset -> init -> begin -> WHILE(step){ split -> scan -> compact ->
+//   WHILE(pass){ search -> pass_end } -> advance -> step_end } -> finalize
+template <int W, int S>
+cudaError_t build_graph(Plan &pl, Dev<W> d, const Geometry &g)
+{
+    cudaGraph_t G;
+    cudaError_t e = cudaGraphCreate(&G, 0);
+    if (e != cudaSuccess)
+        return e;
+    pl.graph = G;
+    cudaGraphConditionalHandle hs, hp;
+    if ((e = cudaGraphConditionalHandleCreate(&hs, G, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return e;
+    d.graph = 1;
+    d.h_step = hs;
+    d.h_pass = 0;
+    const dim3 one(1), b128(128), b256(256), b1024(1024);
+    const dim3 g_inst((g.n_cap + 127) / 128), g_prob(g.n_cap);
+    cudaGraphNode_t n_reset, n_init, n_begin, n_step, n_fin;
+    if ((e = add_kernel(&n_reset, G, nullptr, 0, k_reset<W>, one, one, 0, d)) != cudaSuccess)
+        return e;
+    if ((e = add_kernel(&n_init, G, &n_reset, 1, k_init<W>, g_inst, b128, 0, d)) != cudaSuccess)
+        return e;
+    if ((e = add_kernel(&n_begin, G, &n_init, 1, k_begin<W>, one, one, 0, d)) != cudaSuccess)
+        return e;
+    cudaGraph_t B;
+    if ((e = add_while(&n_step, G, &n_begin, 1, hs, &B)) != cudaSuccess)
+        return e;
+    if ((e = add_kernel(&n_fin, G, &n_step, 1, k_finalize<W>, g_inst, b128, 0, d)) != cudaSuccess)
+        return e;
+
+    if ((e = cudaGraphConditionalHandleCreate(&hp, B, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return e;
+    d.h_pass = hp;
+    cudaGraphNode_t n_split, n_scan, n_compact, n_pass, n_adv, n_send;
+    if ((e = add_kernel(&n_split, B, nullptr, 0, k_split<W>, g_prob, b256, 0, d)) != cudaSuccess)
+        return e;
+    if ((e = add_kernel(&n_scan, B, &n_split, 1, k_scan<W>, one, b1024, 0, d)) != cudaSuccess)
+        return e;
+    if ((e = add_kernel(&n_compact, B, &n_scan, 1, k_compact<W>, g_prob, b128, 0, d)) != cudaSuccess)
+        return e;
+    cudaGraph_t P;
+    if ((e = add_while(&n_pass, B, &n_compact, 1, hp, &P)) != cudaSuccess)
+        return e;
+    if ((e = add_kernel(&n_adv, B, &n_pass, 1, k_advance<W>, g_inst, b128, 0, d)) != cudaSuccess)
+        return e;
+    if ((e = add_kernel(&n_send, B, &n_adv, 1, k_step_end<W>, one, one, 0, d)) != cudaSuccess)
+        return e;
+
+    cudaGraphNode_t n_search, n_pend;
+    if ((e = add_kernel(&n_search, P, nullptr, 0, k_search<W, S>, dim3(g.grid), dim3(g.threads), g.smem, d)) !=
+        cudaSuccess)
+        return e;
+    if ((e = add_kernel(&n_pend, P, &n_search, 1, k_pass_end<W>, one, one, 0, d)) != cudaSuccess)
+        return e;
+    return cudaGraphInstantiate(&pl.exec, G, 0);
+}
+
 template <int W, int S>
 bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_len, uint8_t *out_moves,
                  uint64_t *out_nodes, int *out_iters, int *out_status, cudaStream_t st)
 {
-    typedef typename Geo<W>::B B;
     int dev = 0;
     CK(cudaGetDevice(&dev));
     Workspace &ws = *workspace_for(dev);
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
 
-    const int wpb = cfg.wpb;
-    const int threads = wpb * 32;
-    const size_t smem = SharedLut<W>::BYTES + (size_t)wpb * S * WarpStack<W>::ENTRY_BYTES;
-    CK(cudaFuncSetAttribute(k_search<W, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    Geometry g;
+    g.n_cap = n;
+    g.threads = cfg.wpb * 32;
+    g.smem = SharedLut<W>::BYTES + (size_t)cfg.wpb * S * WarpStack<W>::ENTRY_BYTES;
+    CK(cudaFuncSetAttribute(k_search<W, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem));
     int bpsm = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_search<W, S>, threads, smem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_search<W, S>, g.threads, g.smem));
     if (bpsm < 1)
         return BPIDA_EINVAL;
-    const int grid = sms * bpsm;
-    const int total_warps = grid * wpb;
-
-    int tcap = cfg.split_target;
-    if (tcap <= 0)
-        tcap = std::max(2, std::min(16384, (1 << 21) / std::max(n, 1)));
-    const int C = 4 * tcap + 4;
-    const size_t nrec_region = (size_t)n * 2 * C;
+    g.grid = sms * bpsm;
+    g.total_warps = g.grid * cfg.wpb;
+    g.tcap = cfg.split_target > 0 ? cfg.split_target : std::max(2, std::min(16384, (1 << 21) / std::max(n, 1)));
+    g.C = 4 * g.tcap + 4;
     // hand-back queue: every warp's stack plus its unfinished chunk, with
-    // room for overflow spills (each spill moves S/2 entries); overflowing it
-    // is detected and reported as BPIDA_ENOMEM
-    const size_t Q = std::max({(size_t)n * C, (size_t)total_warps * (S + 32) * 4, (size_t)1 << 24}) + 1024;
-    if (Q > (size_t)INT_MAX / 2)
+    // room for overflow spills (each moves S/2 entries); overflowing it is
+    // detected and reported as BPIDA_ENOMEM
+    g.Q = std::max({(size_t)n * g.C, (size_t)g.total_warps * (S + 32) * 4, (size_t)1 << 24}) + 1024;
+    if (g.Q > (size_t)INT_MAX / 2 || (size_t)n * 2 * g.C > (size_t)UINT32_MAX)
         return BPIDA_ENOMEM;
 
-    CK(ensure(ws.state, sizeof(InstState<W>) * n));
-    CK(ensure(ws.act0, sizeof(unsigned) * n));
-    CK(ensure(ws.act1, sizeof(unsigned) * n));
-    const size_t ctr_bytes = (size_t)n * (3 * sizeof(unsigned long long) + sizeof(int) + sizeof(unsigned));
-    CK(ensure(ws.ctr, ctr_bytes));
-    CK(ensure(ws.scratch, sizeof(Rec<W>) * nrec_region));
-    CK(ensure(ws.count, sizeof(int) * n));
-    CK(ensure(ws.offset, sizeof(int) * n));
-    CK(ensure(ws.q0, sizeof(Rec<W>) * Q));
-    CK(ensure(ws.q1, sizeof(Rec<W>) * Q));
-    CK(ensure(ws.ctrl, sizeof(Ctrl)));
+    CK(ws.ensure(ws.state, sizeof(InstState<W>) * n));
+    CK(ws.ensure(ws.act0, sizeof(unsigned) * n));
+    CK(ws.ensure(ws.act1, sizeof(unsigned) * n));
+    CK(ws.ensure(ws.ctr, (size_t)n * (3 * sizeof(unsigned long long) + sizeof(int) + sizeof(unsigned))));
+    CK(ws.ensure(ws.scratch, sizeof(Rec<W>) * (size_t)n * 2 * g.C));
+    CK(ws.ensure(ws.count, sizeof(int) * n));
+    CK(ws.ensure(ws.offset, sizeof(int) * n));
+    CK(ws.ensure(ws.q0, sizeof(Rec<W>) * g.Q));
+    CK(ws.ensure(ws.q1, sizeof(Rec<W>) * g.Q));
+    CK(ws.ensure(ws.ctrl, sizeof(Ctrl)));
+    CK(ws.ensure(ws.desc, sizeof(CallDesc)));
     if (!ws.h_ctrl)
         CK(cudaMallocHost((void **)&ws.h_ctrl, sizeof(Ctrl)));
     if (!ws.ev0) {
@@ -177,122 +300,142 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
         CK(cudaEventCreate(&ws.ev1));
     }
 
-    Counters cnt;
+    Dev<W> d;
+    std::memset(&d, 0, sizeof d);
+    d.ctrl = (Ctrl *)ws.ctrl.p;
+    d.desc = (const CallDesc *)ws.desc.p;
+    d.state = (InstState<W> *)ws.state.p;
+    d.act0 = (unsigned *)ws.act0.p;
+    d.act1 = (unsigned *)ws.act1.p;
+    d.scratch = (Rec<W> *)ws.scratch.p;
+    d.q0 = (Rec<W> *)ws.q0.p;
+    d.q1 = (Rec<W> *)ws.q1.p;
+    d.count = (int *)ws.count.p;
+    d.offset = (int *)ws.offset.p;
+    d.C = g.C;
+    d.Q = (int)g.Q;
     {
         char *p = (char *)ws.ctr.p;
-        cnt.search_nodes = (unsigned long long *)p;
+        d.cnt.search_nodes = (unsigned long long *)p;
         p += sizeof(unsigned long long) * n;
-        cnt.split_nodes = (unsigned long long *)p;
+        d.cnt.split_nodes = (unsigned long long *)p;
         p += sizeof(unsigned long long) * n;
-        cnt.goals = (unsigned long long *)p;
+        d.cnt.goals = (unsigned long long *)p;
         p += sizeof(unsigned long long) * n;
-        cnt.fnext_off = (int *)p;
+        d.cnt.fnext_off = (int *)p;
         p += sizeof(int) * n;
-        cnt.goal_origin = (unsigned *)p;
+        d.cnt.goal_origin = (unsigned *)p;
     }
-    Tune tune;
-    tune.min_rounds = cfg.min_rounds;
-    tune.exit_threshold = std::max(1, (int)((long long)total_warps * cfg.exit_pct / 100));
-    tune.nodes_per_record = 4096;
-    tune.target_cap = tcap;
-    tune.target_path = std::min(tcap, 4096);
-    tune.growth = 8;
+    d.tune.min_rounds = cfg.min_rounds;
+    d.tune.exit_threshold = std::max(1, (int)((long long)g.total_warps * cfg.exit_pct / 100));
+    d.tune.nodes_per_record = 4096;
+    d.tune.target_cap = g.tcap;
+    d.tune.target_path = std::min(g.tcap, 4096);
+    d.tune.growth = 8;
+    d.lut = make_lut<W>();
 
-    const MoveLut<W> lut = make_lut<W>();
-    Ctrl *ctrl = (Ctrl *)ws.ctrl.p;
-    InstState<W> *state = (InstState<W> *)ws.state.p;
-    unsigned *act[2] = {(unsigned *)ws.act0.p, (unsigned *)ws.act1.p};
-    Rec<W> *scratch = (Rec<W> *)ws.scratch.p;
-    Rec<W> *q[2] = {(Rec<W> *)ws.q0.p, (Rec<W> *)ws.q1.p};
-    int *count = (int *)ws.count.p, *offset = (int *)ws.offset.p;
+    CallDesc desc;
+    std::memset(&desc, 0, sizeof desc);
+    desc.boards = boards;
+    desc.out_len = out_len;
+    desc.out_moves = out_moves;
+    desc.out_nodes = (unsigned long long *)out_nodes;
+    desc.out_iters = out_iters;
+    desc.out_status = out_status;
+    desc.node_budget = cfg.budget;
+    desc.n = n;
+    k_set_desc<<<1, 1, 0, st>>>(desc, (CallDesc *)ws.desc.p);
+    CK(cudaGetLastError());
 
     bpida_stats stats;
     std::memset(&stats, 0, sizeof stats);
-    stats.grid_blocks = grid;
-    stats.block_threads = threads;
+    stats.grid_blocks = g.grid;
+    stats.block_threads = g.threads;
     stats.sm_count = sms;
 
-    CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
-    {
-        InitArgs<W> ia{boards, n, state, act[0], ctrl, out_moves, (unsigned long long *)out_nodes};
-        k_init<W><<<(n + 127) / 128, 128, 0, st>>>(ia);
-        CK(cudaGetLastError());
-        stats.launches++;
-    }
-    CK(cudaMemcpyAsync(ws.h_ctrl, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    int n_active = ws.h_ctrl->n_active;
-    int cur = 0;
-    bpida_status abort_status = BPIDA_OK;
-
-    while (n_active > 0) {
-        SplitArgs<W> sa{act[cur], state, scratch, C, count, cnt, lut};
-        k_split<W><<<n_active, 256, 0, st>>>(sa);
-        CK(cudaGetLastError());
-        k_scan<<<1, 1024, 0, st>>>(count, offset, ctrl);
-        CK(cudaGetLastError());
-        k_compact<W><<<n_active, 128, 0, st>>>(scratch, C, count, offset, q[0]);
-        CK(cudaGetLastError());
-        stats.launches += 3;
-        int qi = 0;
-        for (;;) {
-            SearchArgs<W> a{q[qi], q[qi ^ 1], (int)Q, ctrl, cnt, tune, lut};
-            if (g_timing)
-                CK(cudaEventRecord(ws.ev0, st));
-            k_search<W, S><<<grid, threads, smem, st>>>(a);
-            CK(cudaGetLastError());
-            if (g_timing)
-                CK(cudaEventRecord(ws.ev1, st));
-            stats.passes++;
-            stats.launches++;
-            CK(cudaMemcpyAsync(ws.h_ctrl, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            if (g_timing) {
-                float ms = 0.f;
-                CK(cudaEventElapsedTime(&ms, ws.ev0, ws.ev1));
-                stats.search_ms += ms;
+    const dim3 one(1), b128(128), b256(256), b1024(1024);
+    const dim3 g_inst((n + 127) / 128);
+    if (cfg.driver == 0) {
+        const PlanKey key(W, S, cfg.wpb, n, g.tcap, cfg.exit_pct, cfg.min_rounds);
+        Plan &pl = ws.plans[key];
+        if (pl.exec && pl.gen != ws.gen)
+            pl.destroy();
+        if (!pl.exec) {
+            cudaError_t e = build_graph<W, S>(pl, d, g);
+            if (e != cudaSuccess) {
+                std::fprintf(stderr, "bpida: graph build failed: %s\n", cudaGetErrorString(e));
+                pl.destroy();
+                return BPIDA_ECUDA;
             }
-            if (ws.h_ctrl->err & ERR_QUEUE) {
-                abort_status = BPIDA_ENOMEM;
-                break;
-            }
-            if (ws.h_ctrl->out_count == 0)
-                break;
-            k_next_pass<<<1, 1, 0, st>>>(ctrl);
-            CK(cudaGetLastError());
-            stats.launches++;
-            qi ^= 1;
+            pl.gen = ws.gen;
         }
-        if (abort_status != BPIDA_OK)
-            break;
-        AdvanceArgs<W> aa{act[cur], act[cur ^ 1], state, scratch, C, count, offset, cnt, ctrl, tune,
-                          (unsigned long long)cfg.budget, out_moves, (unsigned long long *)out_nodes};
-        k_advance<W><<<(n_active + 127) / 128, 128, 0, st>>>(aa);
-        CK(cudaGetLastError());
-        k_step_end<<<1, 1, 0, st>>>(ctrl);
-        CK(cudaGetLastError());
-        stats.launches += 2;
-        CK(cudaMemcpyAsync(ws.h_ctrl, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+        CK(cudaGraphLaunch(pl.exec, st));
+        CK(cudaMemcpyAsync(ws.h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        stats.steps++;
-        n_active = ws.h_ctrl->n_active;
-        cur ^= 1;
+        stats.launches = 1 + 4 + 5 * ws.h_ctrl->steps + 2 * (int)ws.h_ctrl->passes_total;
+    } else {
+        // host-driven loop over the same kernels
+        d.graph = 0;
+        k_reset<W><<<1, 1, 0, st>>>(d);
+        k_init<W><<<g_inst, b128, 0, st>>>(d);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(ws.h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        stats.launches = 3;
+        int n_active = ws.h_ctrl->n_active;
+        while (n_active > 0) {
+            k_split<W><<<n_active, b256, 0, st>>>(d);
+            k_scan<W><<<1, b1024, 0, st>>>(d);
+            k_compact<W><<<n_active, b128, 0, st>>>(d);
+            CK(cudaGetLastError());
+            stats.launches += 3;
+            for (;;) {
+                if (g_timing)
+                    CK(cudaEventRecord(ws.ev0, st));
+                k_search<W, S><<<g.grid, g.threads, g.smem, st>>>(d);
+                CK(cudaGetLastError());
+                if (g_timing)
+                    CK(cudaEventRecord(ws.ev1, st));
+                k_pass_end<W><<<1, 1, 0, st>>>(d);
+                CK(cudaGetLastError());
+                stats.launches += 2;
+                CK(cudaMemcpyAsync(ws.h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                if (g_timing) {
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, ws.ev0, ws.ev1));
+                    stats.search_ms += ms;
+                }
+                if (!ws.h_ctrl->pass_again)
+                    break;
+            }
+            k_advance<W><<<(n_active + 127) / 128, b128, 0, st>>>(d);
+            k_step_end<W><<<1, 1, 0, st>>>(d);
+            CK(cudaGetLastError());
+            stats.launches += 2;
+            CK(cudaMemcpyAsync(ws.h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            n_active = ws.h_ctrl->step_again ? ws.h_ctrl->n_active : 0;
+        }
+        k_finalize<W><<<g_inst, b128, 0, st>>>(d);
+        CK(cudaGetLastError());
+        stats.launches += 1;
+        CK(cudaMemcpyAsync(ws.h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
     }
-    k_finalize<W><<<(n + 127) / 128, 128, 0, st>>>(state, n, out_len, out_iters, out_status,
-                                                   (int)abort_status);
-    CK(cudaGetLastError());
-    stats.launches++;
-    CK(cudaMemcpyAsync(ws.h_ctrl, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    stats.records = ws.h_ctrl->records_total;
-    stats.handed_back = ws.h_ctrl->handed_back_total;
-    stats.search_nodes = ws.h_ctrl->search_nodes_total;
-    stats.spills = ws.h_ctrl->spills;
-    stats.max_handed_back = ws.h_ctrl->max_out;
+    const Ctrl &c = *ws.h_ctrl;
+    stats.steps = c.steps;
+    stats.passes = (int)c.passes_total;
+    stats.records = c.records_total;
+    stats.handed_back = c.handed_back_total;
+    stats.search_nodes = c.search_nodes_total;
+    stats.spills = c.spills;
+    stats.max_handed_back = c.max_out;
+    stats.search_ms_device = (double)c.search_ns * 1e-6;
     g_stats = stats;
-    if (abort_status != BPIDA_OK)
-        return abort_status;
-    if (ws.h_ctrl->err & ERR_INTERNAL)
+    if (c.err & ERR_QUEUE)
+        return BPIDA_ENOMEM;
+    if (c.err)
         return BPIDA_EINTERNAL;
     return BPIDA_OK;
 }
@@ -344,12 +487,15 @@ bpida_status bpida_solve_ex(const bpida_config *cfg_in, const uint64_t *boards, 
     cfg.S = (cfg_in && cfg_in->stack_entries > 0) ? cfg_in->stack_entries : 512;
     cfg.exit_pct = (cfg_in && cfg_in->exit_fraction_pct > 0) ? cfg_in->exit_fraction_pct : 25;
     cfg.min_rounds = (cfg_in && cfg_in->min_rounds > 0) ? cfg_in->min_rounds : 64;
+    cfg.driver = cfg_in ? cfg_in->driver : 0;
     cfg.budget = cfg_in ? cfg_in->node_budget : 0;
     if (cfg.width < 3 || cfg.width > 5 || n < 0)
         return BPIDA_EINVAL;
     if (cfg.S != 256 && cfg.S != 512 && cfg.S != 1024)
         return BPIDA_EINVAL;
-    if (cfg.wpb < 1 || cfg.wpb > 32 || cfg.exit_pct > 100 || cfg.split_target < 0)
+    if (cfg.wpb < 1 || cfg.wpb > 32 || cfg.exit_pct > 100 || cfg.split_target < 0 || cfg.split_target > (1 << 20))
+        return BPIDA_EINVAL;
+    if (cfg.driver != 0 && cfg.driver != 1)
         return BPIDA_EINVAL;
     if (cfg.count_all != 1)
         return BPIDA_EINVAL;  // only the all-solutions mode is implemented

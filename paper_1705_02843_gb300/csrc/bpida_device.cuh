@@ -148,7 +148,7 @@ template <int W> __device__ __forceinline__ int move_off(int m)
     return m == 0 ? -W : m == 1 ? -1 : m == 2 ? 1 : W;
 }
 
-// ---- shared control block ----
+// ---- control block (device memory; the loop state of one solve call) ----
 struct Ctrl {
     int n_in;         // records in this pass's input queue
     int head;         // next input record to take
@@ -157,14 +157,37 @@ struct Ctrl {
     int err;          // error bits (ERR_*)
     int n_active;     // problems in this step
     int n_next;       // problems for the next step
-    int pad;
+    int cur;          // which active list holds this step's problems
+    int qi;           // which queue is this pass's input
+    int steps;        // threshold steps completed
+    int passes_step;  // search passes in this step
+    int max_out;      // largest hand-back of one pass
+    int pass_again;   // set by k_pass_end: another pass follows
+    int step_again;   // set by k_step_end: another step follows
     unsigned long long records_total;
     unsigned long long handed_back_total;
     unsigned long long search_nodes_total;  // nodes popped by k_search
-    unsigned long long spills;               // stack overflows handed back
-    int max_out;                             // largest hand-back of one pass
-    int pad2;
+    unsigned long long spills;              // stack overflows handed back
+    unsigned long long passes_total;
+    unsigned long long search_ns;           // sum of k_search durations (globaltimer)
+    unsigned long long t_start, t_end;      // this pass's first block start / last block end
 };
+static constexpr int MAX_STEPS = 100000;        // loop guards: exceeding one is an
+static constexpr int MAX_PASSES_PER_STEP = 100000;  // internal error, never a hang
+
+// ---- one call's arguments (device memory, written before the loop) ----
+struct CallDesc {
+    const uint64_t *boards;
+    int *out_len;
+    uint8_t *out_moves;
+    unsigned long long *out_nodes;
+    int *out_iters;
+    int *out_status;
+    unsigned long long node_budget;
+    int n;
+    int pad;
+};
+
 static constexpr int ERR_QUEUE = 1;      // hand-back queue full
 static constexpr int ERR_INTERNAL = 2;   // consistency check failed
 
@@ -260,17 +283,31 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *warp_sums, int *
 }
 
 // ---------------------------------------------------------------------
-// Search kernel: persistent warps, one subtree group per warp.
+// Device view of one solve call's workspace, passed to every kernel.
 // ---------------------------------------------------------------------
-template <int W> struct SearchArgs {
-    const Rec<W> *in;
-    Rec<W> *out;
-    int out_cap;
+template <int W> struct Dev {
     Ctrl *ctrl;
+    const CallDesc *desc;
+    InstState<W> *state;
+    unsigned *act0, *act1;      // active problem lists (ctrl->cur selects)
+    Rec<W> *scratch;            // per problem: 2 * C records
+    Rec<W> *q0, *q1;            // pass queues (ctrl->qi selects the input)
+    int *count, *offset;        // per problem: final-level records, prefix
+    int C;
+    int Q;                      // capacity of each queue
     Counters cnt;
     Tune tune;
     MoveLut<W> lut;
+    cudaGraphConditionalHandle h_step, h_pass;
+    int graph;                  // 1 inside the CUDA graph (sets the loop conditions)
 };
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // ---- warp stack entries ----
 // Stack metadata (32 bits), different from the record metadata:
@@ -381,8 +418,8 @@ template <int W> __device__ __forceinline__ bool away_bit(const LutRow<W> &row, 
 }
 
 template <int W, int S>
-__device__ __forceinline__ void hand_back_stack(const SearchArgs<W> &a, const WarpStack<W> &stk, int from,
-                                                int k, unsigned inst, int lane)
+__device__ __forceinline__ void hand_back_stack(const Dev<W> &a, Rec<W> *out, const WarpStack<W> &stk,
+                                                int from, int k, unsigned inst, int lane)
 {
     if (k <= 0)
         return;
@@ -390,7 +427,7 @@ __device__ __forceinline__ void hand_back_stack(const SearchArgs<W> &a, const Wa
     if (lane == 0)
         base = atomicAdd(&a.ctrl->out_count, k);
     base = __shfl_sync(FULL, base, 0);
-    if (base + k > a.out_cap) {
+    if (base + k > a.Q) {
         if (lane == 0)
             atomicOr(&a.ctrl->err, ERR_QUEUE);
         return;
@@ -405,12 +442,13 @@ __device__ __forceinline__ void hand_back_stack(const SearchArgs<W> &a, const Wa
         r.inst = inst;
         r.origin = o;
         r.pm = 0;
-        a.out[base + j] = r;
+        out[base + j] = r;
     }
 }
 
 template <int W>
-__device__ __forceinline__ void hand_back_records(const SearchArgs<W> &a, int from, int to, int lane)
+__device__ __forceinline__ void hand_back_records(const Dev<W> &a, const Rec<W> *in, Rec<W> *out, int from,
+                                                  int to, int lane)
 {
     const int k = to - from;
     if (k <= 0)
@@ -419,13 +457,13 @@ __device__ __forceinline__ void hand_back_records(const SearchArgs<W> &a, int fr
     if (lane == 0)
         base = atomicAdd(&a.ctrl->out_count, k);
     base = __shfl_sync(FULL, base, 0);
-    if (base + k > a.out_cap) {
+    if (base + k > a.Q) {
         if (lane == 0)
             atomicOr(&a.ctrl->err, ERR_QUEUE);
         return;
     }
     for (int j = lane; j < k; j += 32)
-        a.out[base + j] = a.in[from + j];
+        out[base + j] = in[from + j];
 }
 
 // One warp = one shared stack (Algorithm 1's openList). Each round pops up
@@ -436,14 +474,18 @@ __device__ __forceinline__ void hand_back_records(const SearchArgs<W> &a, int fr
 // records from the pass's input queue until it is exhausted; once enough
 // warps have run dry, busy warps hand their open nodes to the next pass.
 template <int W, int S>
-__global__ void k_search(const SearchArgs<W> a)
+__global__ void k_search(const Dev<W> a)
 {
     typedef typename Geo<W>::B B;
     constexpr int BITS = Geo<W>::BITS;
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char *lut = smem;
+    if (threadIdx.x == 0)
+        atomicMin(&a.ctrl->t_start, global_ns());
     SharedLut<W>::load(lut, a.lut);
     __syncthreads();
+    const Rec<W> *in = a.ctrl->qi ? a.q1 : a.q0;
+    Rec<W> *out = a.ctrl->qi ? a.q0 : a.q1;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpStack<W> stk;
@@ -471,7 +513,7 @@ __global__ void k_search(const SearchArgs<W> a)
             const bool v = idx < end;
             Rec<W> r;
             if (v)
-                r = a.in[idx];
+                r = in[idx];
             const unsigned inst = v ? r.inst : 0xffffffffu;
             const unsigned inst0 = __shfl_sync(FULL, inst, 0);
             const unsigned same = __ballot_sync(FULL, v && inst == inst0);
@@ -493,7 +535,7 @@ __global__ void k_search(const SearchArgs<W> a)
                     const int k = min(size - n, S / 2);
                     if (lane == 0)
                         atomicAdd(&a.ctrl->spills, 1ull);
-                    hand_back_stack<W, S>(a, stk, bot, k, inst0, lane);
+                    hand_back_stack<W, S>(a, out, stk, bot, k, inst0, lane);
                     bot += k;
                     __syncwarp();
                 }
@@ -566,8 +608,8 @@ __global__ void k_search(const SearchArgs<W> a)
                     atomicMin(&a.cnt.fnext_off[inst0], fmin);
             }
             if (stop) {
-                hand_back_stack<W, S>(a, stk, bot, top - bot, inst0, lane);
-                hand_back_records<W>(a, i + cnt, end, lane);
+                hand_back_stack<W, S>(a, out, stk, bot, top - bot, inst0, lane);
+                hand_back_records<W>(a, in, out, i + cnt, end, lane);
                 break;
             }
             i += cnt;
@@ -577,24 +619,19 @@ __global__ void k_search(const SearchArgs<W> a)
     }
     if (!stop && lane == 0)
         atomicAdd(&a.ctrl->exited, 1);
+    __syncthreads();
+    if (threadIdx.x == 0)
+        atomicMax(&a.ctrl->t_end, global_ns());
 }
 
 // ---------------------------------------------------------------------
 // Splitter: one block per problem; breadth-first, order-preserving
-// expansion of the problem's root until the level holds `target` records.
+// expansion of the problem's root until the level holds `target` records
+// (Algorithm 1's CreateRootSet, rebuilt every iteration). Nodes expanded
+// here are counted here; the final level becomes the problem's frontier.
 // ---------------------------------------------------------------------
-template <int W> struct SplitArgs {
-    const unsigned *active;
-    InstState<W> *state;
-    Rec<W> *scratch;     // per problem: 2 * C records
-    int C;
-    int *count;          // records in the problem's final level
-    Counters cnt;
-    MoveLut<W> lut;
-};
-
 template <int W>
-__global__ void k_split(const SplitArgs<W> a)
+__global__ void k_split(const Dev<W> a)
 {
     typedef typename Geo<W>::B B;
     constexpr int BITS = Geo<W>::BITS;
@@ -602,10 +639,12 @@ __global__ void k_split(const SplitArgs<W> a)
     __shared__ int warp_sums[32];
     __shared__ int s_fmin, s_leaves_only;
     __shared__ unsigned long long s_internal;
-    SharedLut<W>::load(lut, a.lut);
 
     const int k = blockIdx.x;
-    const unsigned inst = a.active[k];
+    if (k >= a.ctrl->n_active)
+        return;
+    SharedLut<W>::load(lut, a.lut);
+    const unsigned inst = (a.ctrl->cur ? a.act1 : a.act0)[k];
     const InstState<W> st = a.state[inst];
     Rec<W> *A = a.scratch + (size_t)k * 2 * a.C;
     Rec<W> *Bf = A + a.C;
@@ -698,11 +737,9 @@ __global__ void k_split(const SplitArgs<W> a)
                 nxt[outbase + pos + q] = c[q];
             outbase += total;
         }
-        // block reductions of the level's counters
         fmin = warp_min_int(fmin);
-        if ((threadIdx.x & 31) == 0) {
+        if ((threadIdx.x & 31) == 0)
             atomicMin(&s_fmin, fmin);
-        }
         for (int d2 = 16; d2; d2 >>= 1)
             internal += __shfl_xor_sync(FULL, internal, d2);
         if ((threadIdx.x & 31) == 0)
@@ -725,22 +762,25 @@ __global__ void k_split(const SplitArgs<W> a)
     }
 }
 
-// Exclusive scan of the per-problem record counts (one block).
-__global__ void k_scan(const int *count, int *offset, Ctrl *ctrl)
+// Exclusive scan of the per-problem record counts (one block); opens the
+// step's first search pass.
+template <int W>
+__global__ void k_scan(const Dev<W> a)
 {
     __shared__ int warp_sums[32];
     __shared__ int carry;
+    Ctrl *ctrl = a.ctrl;
     const int n = ctrl->n_active;
     if (threadIdx.x == 0)
         carry = 0;
     __syncthreads();
     for (int base = 0; base < n; base += blockDim.x) {
         const int j = base + threadIdx.x;
-        const int v = j < n ? count[j] : 0;
+        const int v = j < n ? a.count[j] : 0;
         int total;
         const int pos = block_exclusive_scan(v, warp_sums, &total);
         if (j < n)
-            offset[j] = carry + pos;
+            a.offset[j] = carry + pos;
         __syncthreads();
         if (threadIdx.x == 0)
             carry += total;
@@ -751,58 +791,67 @@ __global__ void k_scan(const int *count, int *offset, Ctrl *ctrl)
         ctrl->head = 0;
         ctrl->out_count = 0;
         ctrl->exited = 0;
+        ctrl->qi = 0;
+        ctrl->passes_step = 0;
+        ctrl->t_start = ~0ull;
+        ctrl->t_end = 0;
         ctrl->records_total += (unsigned long long)carry;
+        if (a.graph)
+            cudaGraphSetConditional(a.h_pass, 1u);
     }
 }
 
 // Gather every problem's frontier into the first pass's queue; a record's
 // origin is its position in that queue.
 template <int W>
-__global__ void k_compact(const Rec<W> *scratch, int C, const int *count, const int *offset,
-                          Rec<W> *q)
+__global__ void k_compact(const Dev<W> a)
 {
     const int k = blockIdx.x;
-    const Rec<W> *A = scratch + (size_t)k * 2 * C;
-    const int n = count[k], o = offset[k];
+    if (k >= a.ctrl->n_active)
+        return;
+    const Rec<W> *A = a.scratch + (size_t)k * 2 * a.C;
+    const int n = a.count[k], o = a.offset[k];
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         Rec<W> r = A[j];
         r.origin = (uint32_t)(o + j);
-        q[o + j] = r;
+        a.q0[o + j] = r;
     }
 }
 
-// Between passes: the records handed back become the next input.
-__global__ void k_next_pass(Ctrl *ctrl)
+// After a search pass: the records handed back become the next pass's
+// input; the pass loop ends when nothing was handed back.
+template <int W>
+__global__ void k_pass_end(const Dev<W> a)
 {
-    ctrl->max_out = max(ctrl->max_out, ctrl->out_count);
-    ctrl->n_in = ctrl->out_count;
-    ctrl->handed_back_total += (unsigned long long)ctrl->out_count;
-    ctrl->head = 0;
-    ctrl->out_count = 0;
-    ctrl->exited = 0;
+    Ctrl *c = a.ctrl;
+    c->passes_step += 1;
+    c->passes_total += 1;
+    if (c->t_end > c->t_start)
+        c->search_ns += c->t_end - c->t_start;
+    c->t_start = ~0ull;
+    c->t_end = 0;
+    c->max_out = max(c->max_out, c->out_count);
+    if (c->passes_step >= MAX_PASSES_PER_STEP)
+        c->err |= ERR_INTERNAL;
+    const bool again = c->out_count > 0 && c->err == 0;
+    c->pass_again = again ? 1 : 0;
+    if (again) {
+        c->n_in = c->out_count;
+        c->handed_back_total += (unsigned long long)c->out_count;
+        c->head = 0;
+        c->out_count = 0;
+        c->exited = 0;
+        c->qi ^= 1;
+    }
+    if (a.graph)
+        cudaGraphSetConditional(a.h_pass, again ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------
 // Advance: per problem, close the iteration (Algorithm 1's driver).
 // ---------------------------------------------------------------------
-template <int W> struct AdvanceArgs {
-    const unsigned *active;
-    unsigned *next_active;
-    InstState<W> *state;
-    const Rec<W> *scratch;
-    int C;
-    const int *count;
-    const int *offset;
-    Counters cnt;
-    Ctrl *ctrl;
-    Tune tune;
-    unsigned long long node_budget;
-    uint8_t *out_moves;
-    unsigned long long *out_nodes;
-};
-
 template <int W>
-__device__ bool take_goal_record(const AdvanceArgs<W> &a, int k, unsigned inst, InstState<W> &st)
+__device__ bool take_goal_record(const Dev<W> &a, const CallDesc &dsc, int k, unsigned inst, InstState<W> &st)
 {
     const unsigned go = a.cnt.goal_origin[inst];
     const int local = (int)go - a.offset[k];
@@ -816,7 +865,7 @@ __device__ bool take_goal_record(const AdvanceArgs<W> &a, int k, unsigned inst, 
     if (r.b == goal_board<W>() && st.path_len + d != st.limit)
         return false;
     for (int j = 0; j < d; ++j)
-        a.out_moves[(size_t)inst * Geo<W>::MAXLEN + st.path_len + j] = (uint8_t)((r.pm >> (2 * j)) & 3u);
+        dsc.out_moves[(size_t)inst * Geo<W>::MAXLEN + st.path_len + j] = (uint8_t)((r.pm >> (2 * j)) & 3u);
     st.path_len += d;
     if (st.path_len == st.limit) {
         if (r.b != goal_board<W>())
@@ -833,34 +882,37 @@ __device__ bool take_goal_record(const AdvanceArgs<W> &a, int k, unsigned inst, 
 }
 
 template <int W>
-__global__ void k_advance(const AdvanceArgs<W> a)
+__global__ void k_advance(const Dev<W> a)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= a.ctrl->n_active)
+    Ctrl *ctrl = a.ctrl;
+    if (k >= ctrl->n_active || ctrl->err)
         return;
-    const unsigned inst = a.active[k];
+    const CallDesc dsc = *a.desc;
+    const unsigned inst = (ctrl->cur ? a.act1 : a.act0)[k];
+    unsigned *next_active = ctrl->cur ? a.act0 : a.act1;
     InstState<W> st = a.state[inst];
     const unsigned long long total = a.cnt.split_nodes[inst] + a.cnt.search_nodes[inst];
     const unsigned long long goals = a.cnt.goals[inst];
     if (st.mode == MODE_COUNT) {
-        a.out_nodes[(size_t)inst * Geo<W>::MAXIT + st.it] = total;
+        dsc.out_nodes[(size_t)inst * Geo<W>::MAXIT + st.it] = total;
         st.rows = st.it + 1;
         st.cum_nodes += total;
         if (goals > 0) {
             st.length = st.limit;
             st.solutions = goals;
-            if (!take_goal_record<W>(a, k, inst, st)) {
+            if (!take_goal_record<W>(a, dsc, k, inst, st)) {
                 st.mode = MODE_DONE;
                 st.status = 8;  // BPIDA_EINTERNAL
-                atomicOr(&a.ctrl->err, ERR_INTERNAL);
+                atomicOr(&ctrl->err, ERR_INTERNAL);
             }
         } else {
             const int off = a.cnt.fnext_off[inst];
             if (off == INT_MAX || off <= 0) {
                 st.mode = MODE_DONE;
                 st.status = 8;
-                atomicOr(&a.ctrl->err, ERR_INTERNAL);
-            } else if (a.node_budget && st.cum_nodes > a.node_budget) {
+                atomicOr(&ctrl->err, ERR_INTERNAL);
+            } else if (dsc.node_budget && st.cum_nodes > dsc.node_budget) {
                 st.mode = MODE_DONE;
                 st.status = 4;  // BPIDA_EBUDGET
             } else if (st.it + 1 >= Geo<W>::MAXIT || st.limit + off > Geo<W>::MAXLEN) {
@@ -879,55 +931,70 @@ __global__ void k_advance(const AdvanceArgs<W> a)
             }
         }
     } else if (st.mode == MODE_PATH) {
-        if (goals == 0 || !take_goal_record<W>(a, k, inst, st)) {
+        if (goals == 0 || !take_goal_record<W>(a, dsc, k, inst, st)) {
             st.mode = MODE_DONE;
             st.status = 8;
-            atomicOr(&a.ctrl->err, ERR_INTERNAL);
+            atomicOr(&ctrl->err, ERR_INTERNAL);
         }
     }
     a.state[inst] = st;
     if (st.mode != MODE_DONE) {
-        const int j = atomicAdd(&a.ctrl->n_next, 1);
-        a.next_active[j] = inst;
+        const int j = atomicAdd(&ctrl->n_next, 1);
+        next_active[j] = inst;
     }
 }
 
-__global__ void k_step_end(Ctrl *ctrl)
+// End of a threshold step: the problems still active form the next step.
+template <int W>
+__global__ void k_step_end(const Dev<W> a)
 {
-    ctrl->n_active = ctrl->n_next;
-    ctrl->n_next = 0;
+    Ctrl *c = a.ctrl;
+    c->n_active = c->n_next;
+    c->n_next = 0;
+    c->cur ^= 1;
+    c->steps += 1;
+    if (c->steps >= MAX_STEPS)
+        c->err |= ERR_INTERNAL;
+    c->step_again = (c->n_active > 0 && c->err == 0) ? 1 : 0;
+    if (a.graph)
+        cudaGraphSetConditional(a.h_step, (unsigned)c->step_again);
 }
 
 // ---------------------------------------------------------------------
-// Init / finalize
+// Init / begin / finalize
 // ---------------------------------------------------------------------
-template <int W> struct InitArgs {
-    const uint64_t *boards;
-    int n;
-    InstState<W> *state;
-    unsigned *active;
-    Ctrl *ctrl;
-    uint8_t *out_moves;
-    unsigned long long *out_nodes;
-};
+template <int W>
+__global__ void k_reset(const Dev<W> a)
+{
+    Ctrl *c = a.ctrl;
+    if (threadIdx.x == 0) {
+        Ctrl z;
+        memset(&z, 0, sizeof z);
+        z.t_start = ~0ull;
+        *c = z;
+    }
+}
+
+__global__ void k_set_desc(CallDesc d, CallDesc *dst) { *dst = d; }
 
 template <int W>
-__global__ void k_init(const InitArgs<W> a)
+__global__ void k_init(const Dev<W> a)
 {
     typedef typename Geo<W>::B B;
     constexpr int N = Geo<W>::N, BITS = Geo<W>::BITS;
+    const CallDesc dsc = *a.desc;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n)
+    if (i >= dsc.n)
         return;
     for (int j = 0; j < Geo<W>::MAXLEN; ++j)
-        a.out_moves[(size_t)i * Geo<W>::MAXLEN + j] = 0;
+        dsc.out_moves[(size_t)i * Geo<W>::MAXLEN + j] = 0;
     for (int j = 0; j < Geo<W>::MAXIT; ++j)
-        a.out_nodes[(size_t)i * Geo<W>::MAXIT + j] = 0ull;
+        dsc.out_nodes[(size_t)i * Geo<W>::MAXIT + j] = 0ull;
     B b;
     if constexpr (W <= 4) {
-        b = (B)a.boards[i];
+        b = (B)dsc.boards[i];
     } else {
-        b = (B)a.boards[2 * (size_t)i] | ((B)a.boards[2 * (size_t)i + 1] << 64);
+        b = (B)dsc.boards[2 * (size_t)i] | ((B)dsc.boards[2 * (size_t)i + 1] << 64);
     }
     InstState<W> st;
     st.start = b;
@@ -971,51 +1038,51 @@ __global__ void k_init(const InitArgs<W> a)
         const int parity = (W & 1) ? (inv & 1) : ((inv + blank / W) & 1);
         ok = parity == 0;
     }
+    st.start_meta = 0;
+    st.root_meta = 0;
+    st.h0 = ok ? h : -1;
+    st.limit = st.h0;
+    st.mode = MODE_DONE;
     if (!ok) {
-        st.start_meta = 0;
-        st.root_meta = 0;
-        st.h0 = -1;
-        st.limit = -1;
-        st.mode = MODE_DONE;
         st.status = 1;  // BPIDA_EINVAL
-        a.state[i] = st;
-        return;
-    }
-    if (h > Geo<W>::MAXLEN) {
-        st.start_meta = 0;
-        st.root_meta = 0;
-        st.h0 = h;
-        st.limit = h;
-        st.mode = MODE_DONE;
+    } else if (h > Geo<W>::MAXLEN) {
         st.status = 7;  // BPIDA_ELIMIT
-        a.state[i] = st;
-        return;
+    } else {
+        st.start_meta = m_make((uint32_t)blank, LAST_NONE, 0);
+        st.root_meta = st.start_meta;
+        st.mode = MODE_COUNT;
+        st.status = 0;
     }
-    st.h0 = h;
-    st.limit = h;
-    st.start_meta = m_make((uint32_t)blank, LAST_NONE, 0);
-    st.root_meta = st.start_meta;
-    st.mode = MODE_COUNT;
-    st.status = 0;
     a.state[i] = st;
-    const int j = atomicAdd(&a.ctrl->n_active, 1);
-    a.active[j] = (unsigned)i;
+    if (st.mode == MODE_COUNT) {
+        const int j = atomicAdd(&a.ctrl->n_active, 1);
+        a.act0[j] = (unsigned)i;
+    }
 }
 
 template <int W>
-__global__ void k_finalize(const InstState<W> *state, int n, int *out_len, int *out_iters,
-                           int *out_status, int abort_status)
+__global__ void k_begin(const Dev<W> a)
 {
+    if (a.graph)
+        cudaGraphSetConditional(a.h_step, a.ctrl->n_active > 0 ? 1u : 0u);
+}
+
+template <int W>
+__global__ void k_finalize(const Dev<W> a)
+{
+    const CallDesc dsc = *a.desc;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n)
+    if (i >= dsc.n)
         return;
-    const InstState<W> st = state[i];
+    const int err = a.ctrl->err;
+    const int abort_status = (err & ERR_QUEUE) ? 2 : 8;  // BPIDA_ENOMEM or BPIDA_EINTERNAL
+    const InstState<W> st = a.state[i];
     const bool solved = st.mode == MODE_DONE && st.status == 0;
-    out_len[i] = solved ? st.length : -1;
-    if (out_iters)
-        out_iters[i] = st.rows;
-    if (out_status)
-        out_status[i] = st.mode == MODE_DONE ? st.status : (abort_status ? abort_status : 8);
+    dsc.out_len[i] = solved ? st.length : -1;
+    if (dsc.out_iters)
+        dsc.out_iters[i] = st.rows;
+    if (dsc.out_status)
+        dsc.out_status[i] = st.mode == MODE_DONE ? st.status : abort_status;
 }
 
 }  // namespace bp

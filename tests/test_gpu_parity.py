@@ -111,6 +111,7 @@ def test_all_8puzzle_states():
     dict(stack_entries=256), dict(stack_entries=1024), dict(warps_per_block=8),
     dict(split_target=1), dict(split_target=2, min_rounds=32, exit_fraction_pct=1),
     dict(split_target=64, exit_fraction_pct=90),
+    dict(driver=1), dict(driver=1, split_target=1, stack_entries=1024),
 ])
 def test_tuning_knobs_do_not_change_results(cfg):
     insts = I.walks15_16x40()[:8]
@@ -160,3 +161,21 @@ def test_perms15_100_sampled_cheap():
         assert g["nodes"] == r["nodes"]
         assert "".join(map(str, g["moves"])) == r["moves"]
         assert P.replay(4, t, g["moves"]) == list(range(16))
+
+
+def test_graph_and_host_drivers_agree_on_batch():
+    insts = I.walks15_16x40() + [I.make_walk(4, 8800 + i, 30 + i) for i in range(20)]
+    tiles = [x.tiles for x in insts]
+    rc0, a = gpu_solve(4, tiles, driver=0)
+    rc1, b = gpu_solve(4, tiles, driver=1)
+    assert rc0 == rc1 == bpida.OK
+    assert a == b
+
+
+def test_repeated_plain_calls_reuse_the_graph():
+    insts = I.walks15_16x40()[:6]
+    ref = oracle.solve_batch(4, np.array([x.tiles for x in insts], dtype=np.uint8))
+    for x, r in zip(insts, ref):
+        rc, got = gpu_solve(4, [x.tiles])
+        assert rc == bpida.OK
+        assert got[0]["nodes"] == r.nodes and got[0]["moves"] == r.moves
