@@ -51,10 +51,11 @@ WORKLOAD_DESC = ("perms15_100: 100 seeded uniformly random solvable 15-puzzle bo
 
 # Warp instructions issued per node expanded inside k_search<4,512>, from
 # ncu (smsp__inst_executed.sum / nodes) on the one-board capture recorded
-# in profiles/k_search_15puzzle.txt. None until measured.
-INSTR_PER_EXPANSION = None
-# DRAM bytes per k_search launch from the same capture, scaled to the mean
-# launch of this workload; None when not measured for the current kernel.
+# in profiles/k_search_15puzzle_perms15_board0_final_iteration.txt.
+INSTR_PER_EXPANSION = 5.54
+# DRAM bytes per k_search launch; None until measured on this workload's
+# launches for the current kernel (the one-board capture read 136 KB for a
+# 108M-node launch: the kernel is not HBM-bound).
 TRAFFIC_PER_LAUNCH = None
 
 
@@ -195,6 +196,9 @@ def main():
     ap.add_argument("--workload", default="perms15_100", choices=["perms15_100"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-nodes", type=float, default=1.5e9)
+    ap.add_argument("--driver", default="graph", choices=["graph", "host"],
+                    help="graph: each solve call is one CUDA graph launch (default); host: the "
+                         "host launches every kernel (same kernels; ncu can list them)")
     ap.add_argument("--profile-case", type=int, default=None, metavar="IDX",
                     help="solve board IDX alone with one search pass per iteration (for ncu "
                          "captures: the final iteration's k_search launch is number iters-1), "
@@ -225,7 +229,9 @@ def main():
         x = insts[args.profile_case]
         b = torch.from_numpy(I.packed_array([x]).view(np.int64)).to(dev)
         for rep in range(2):
-            s = bpida.solve(b, 4, bpida.make_config(4, exit_fraction_pct=100))
+            # host-driven loop: ncu cannot see kernels inside graphs that
+            # hold conditional nodes
+            s = bpida.solve(b, 4, bpida.make_config(4, exit_fraction_pct=100, driver=1))
             torch.cuda.synchronize(dev)
         h = s.to_host()[0]
         st = bpida.last_stats()
@@ -239,7 +245,10 @@ def main():
     stream = torch.cuda.current_stream(dev)
     bpida.set_timing(True)
 
+    base_cfg = bpida.make_config(4, driver=1 if args.driver == "host" else 0)
+
     def plain_step(cfg=None):
+        cfg = cfg if cfg is not None else base_cfg
         sols, agg = [], {"search_ms": 0.0, "search_ms_device": 0.0, "search_nodes": 0, "passes": 0,
                          "launches": 0}
         for i in range(n):
@@ -253,7 +262,7 @@ def main():
         return sols, agg
 
     def batched_step():
-        s = bpida.solve(boards, 4)
+        s = bpida.solve(boards, 4, base_cfg)
         if s.status != bpida.OK:
             raise RuntimeError("solve failed: " + bpida.status_str(s.status))
         st = bpida.last_stats()
@@ -322,7 +331,7 @@ def main():
         dboards = host_boards.to(dev, non_blocking=True)
         sols = []
         for i in range(n):
-            s = bpida.solve(dboards[i:i + 1], 4)
+            s = bpida.solve(dboards[i:i + 1], 4, base_cfg)
             if s.status != bpida.OK:
                 raise RuntimeError(bpida.status_str(s.status))
             sols.append(s)
@@ -406,6 +415,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_plain * 1e3 / k, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC, "mode": "plain: one solve call per board",
+                       "driver": args.driver,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "flushed between steps (256 MiB write)"},
             "instances_per_s": inst_s,

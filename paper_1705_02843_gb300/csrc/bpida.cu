@@ -273,7 +273,7 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
         return BPIDA_EINVAL;
     g.grid = sms * bpsm;
     g.total_warps = g.grid * cfg.wpb;
-    g.tcap = cfg.split_target > 0 ? cfg.split_target : std::max(2, std::min(16384, (1 << 21) / std::max(n, 1)));
+    g.tcap = cfg.split_target > 0 ? cfg.split_target : std::max(2, std::min(4096, (1 << 21) / std::max(n, 1)));
     g.C = 4 * g.tcap + 4;
     // hand-back queue: every warp's stack plus its unfinished chunk, with
     // room for overflow spills (each moves S/2 entries); overflowing it is
@@ -446,6 +446,8 @@ bpida_status run_w(const Settings &cfg, const uint64_t *boards, int n, int *out_
 {
     switch (cfg.S) {
     case 256: return run<W, 256>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, st);
+    case 384: return run<W, 384>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, st);
+    case 768: return run<W, 768>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, st);
     case 1024: return run<W, 1024>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, st);
     default: return run<W, 512>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, st);
     }
@@ -485,13 +487,13 @@ bpida_status bpida_solve_ex(const bpida_config *cfg_in, const uint64_t *boards, 
     cfg.split_target = cfg_in ? cfg_in->split_target : 0;
     cfg.wpb = (cfg_in && cfg_in->warps_per_block > 0) ? cfg_in->warps_per_block : 4;
     cfg.S = (cfg_in && cfg_in->stack_entries > 0) ? cfg_in->stack_entries : 512;
-    cfg.exit_pct = (cfg_in && cfg_in->exit_fraction_pct > 0) ? cfg_in->exit_fraction_pct : 25;
+    cfg.exit_pct = (cfg_in && cfg_in->exit_fraction_pct > 0) ? cfg_in->exit_fraction_pct : 10;
     cfg.min_rounds = (cfg_in && cfg_in->min_rounds > 0) ? cfg_in->min_rounds : 64;
     cfg.driver = cfg_in ? cfg_in->driver : 0;
     cfg.budget = cfg_in ? cfg_in->node_budget : 0;
     if (cfg.width < 3 || cfg.width > 5 || n < 0)
         return BPIDA_EINVAL;
-    if (cfg.S != 256 && cfg.S != 512 && cfg.S != 1024)
+    if (cfg.S != 256 && cfg.S != 384 && cfg.S != 512 && cfg.S != 768 && cfg.S != 1024)
         return BPIDA_EINVAL;
     if (cfg.wpb < 1 || cfg.wpb > 32 || cfg.exit_pct > 100 || cfg.split_target < 0 || cfg.split_target > (1 << 20))
         return BPIDA_EINVAL;

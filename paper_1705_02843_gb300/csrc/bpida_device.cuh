@@ -311,21 +311,21 @@ __device__ __forceinline__ unsigned long long global_ns()
 
 // ---- warp stack entries ----
 // Stack metadata (32 bits), different from the record metadata:
-//  bits 0..4  blank position
-//  bits 5..8  excluded move mask (the inverse of the move that made the
-//             node; 0 for an instance root)
-//  bits 9..16 slack = limit - g - h
-__device__ __forceinline__ uint32_t sm_from_rec(uint32_t m)
+//  bits 0..6   BITS * blank position (the blank's field offset in the board)
+//  bits 7..10  excluded move mask (the inverse of the move that made the
+//              node; 0 for an instance root)
+//  bits 11..18 slack = limit - g - h
+template <int W> __device__ __forceinline__ uint32_t sm_from_rec(uint32_t m)
 {
     const uint32_t last = m_last(m);
     const uint32_t excl = last < 4u ? (1u << (3u - last)) : 0u;
-    return m_blank(m) | (excl << 5) | ((uint32_t)m_slack(m) << 9);
+    return (m_blank(m) * (uint32_t)Geo<W>::BITS) | (excl << 7) | ((uint32_t)m_slack(m) << 11);
 }
-__device__ __forceinline__ uint32_t rec_from_sm(uint32_t m)
+template <int W> __device__ __forceinline__ uint32_t rec_from_sm(uint32_t m)
 {
-    const uint32_t excl = (m >> 5) & 15u;
+    const uint32_t excl = (m >> 7) & 15u;
     const uint32_t last = excl ? 3u - (uint32_t)(__ffs(excl) - 1) : LAST_NONE;
-    return m_make(m & 31u, last, (m >> 9) & 255u);
+    return m_make((m & 127u) / (uint32_t)Geo<W>::BITS, last, (m >> 11) & 255u);
 }
 
 // W <= 4: one 16-byte entry {board lo, board hi, meta, origin}.
@@ -371,8 +371,9 @@ template <int W> struct WarpStack<W, true> {
     }
 };
 
-// Legal blank moves of every position, 4 bits per position (bit m = move m
-// keeps the blank on the board), as one integer constant.
+// Legal blank moves of every position as one integer constant: the 4-bit
+// mask of position p (bit m = move m keeps the blank on the board) sits at
+// bit BITS*p, so the blank's field offset indexes it directly.
 template <int W> struct LegalMoves {
     typedef typename std::conditional<(W <= 4), uint64_t, u128>::type T;
     __host__ __device__ static constexpr T make()
@@ -381,14 +382,43 @@ template <int W> struct LegalMoves {
         for (int p = 0; p < W * W; ++p) {
             const int r = p / W, c = p % W;
             const unsigned m = (r > 0 ? 1u : 0u) | (c > 0 ? 2u : 0u) | (c < W - 1 ? 4u : 0u) | (r < W - 1 ? 8u : 0u);
-            v |= (T)m << (4 * p);
+            v |= (T)m << (Geo<W>::BITS * p);
         }
         return v;
     }
-    __device__ static __forceinline__ unsigned at(int p)
+    __device__ static __forceinline__ unsigned at_sh(uint32_t sh)
     {
         constexpr T V = make();
-        return (unsigned)(V >> (4 * p)) & 15u;
+        return (unsigned)(V >> sh) & 15u;
+    }
+};
+
+// Field access by bit offset. For 64-bit boards the PTX shifts are used
+// because PTX defines out-of-range amounts (clamped to 64): the offset of an
+// illegal move then yields tile 0 / an unchanged board and needs no select.
+template <int W, bool Wide = (W == 5)> struct BoardOps;
+template <int W> struct BoardOps<W, false> {
+    __device__ static __forceinline__ unsigned tile(uint64_t b, uint32_t sh)
+    {
+        uint64_t r;
+        asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(b), "r"(sh));
+        return (unsigned)r & 15u;
+    }
+    __device__ static __forceinline__ uint64_t flip(uint64_t b, uint32_t v, uint32_t sh)
+    {
+        uint64_t x;
+        asm("shl.b64 %0, %1, %2;" : "=l"(x) : "l"((uint64_t)v), "r"(sh));
+        return b ^ x;
+    }
+};
+template <int W> struct BoardOps<W, true> {
+    __device__ static __forceinline__ unsigned tile(u128 b, uint32_t sh)
+    {
+        return sh < 128u ? ((unsigned)(b >> sh) & 31u) : 0u;
+    }
+    __device__ static __forceinline__ u128 flip(u128 b, uint32_t v, uint32_t sh)
+    {
+        return sh < 128u ? (b ^ ((u128)v << sh)) : b;
     }
 };
 
@@ -399,10 +429,6 @@ template <int W> __device__ __forceinline__ unsigned move_mul(int m)
 {
     constexpr int BITS = Geo<W>::BITS;
     return (m == 0 || m == 3) ? (1u + (1u << (BITS * W))) : (1u + (1u << BITS));
-}
-template <int W> __device__ __forceinline__ int move_low(int m)
-{
-    return m == 0 ? -W : m == 1 ? -1 : 0;  // min(0, off)
 }
 
 // away bit of the Manhattan table row for move m and tile t
@@ -415,6 +441,11 @@ template <int W> __device__ __forceinline__ bool away_bit(const LutRow<W> &row, 
     } else {
         return (row.w(m) >> t) & 1u;
     }
+}
+
+template <int W> __device__ __forceinline__ LutRow<W> lut_row_sh(const unsigned char *base, uint32_t sh)
+{
+    return SharedLut<W>::row(base, (int)(sh / (uint32_t)Geo<W>::BITS));
 }
 
 template <int W, int S>
@@ -435,10 +466,10 @@ __device__ __forceinline__ void hand_back_stack(const Dev<W> &a, Rec<W> *out, co
     for (int j = lane; j < k; j += 32) {
         typename Geo<W>::B b;
         uint32_t m, o;
-        stk.get((from + j) & (S - 1), b, m, o);
+        stk.get(from + j, b, m, o);
         Rec<W> r;
         r.b = b;
-        r.meta = rec_from_sm(m);
+        r.meta = rec_from_sm<W>(m);
         r.inst = inst;
         r.origin = o;
         r.pm = 0;
@@ -519,31 +550,42 @@ __global__ void k_search(const Dev<W> a)
             const unsigned same = __ballot_sync(FULL, v && inst == inst0);
             const int cnt = (same == FULL) ? 32 : (__ffs(~same) - 1);
             if (lane < cnt)
-                stk.put(lane, r.b, sm_from_rec(r.meta), r.origin);
-            int top = cnt, bot = 0;
+                stk.put(lane, r.b, sm_from_rec<W>(r.meta), r.origin);
+            int top = cnt;
             __syncwarp();
             unsigned long long nodes = 0;
             int fmin = INT_MAX;
 
-            while (top != bot) {
-                const int size = top - bot;
-                const int n = min(32, size);
-                if (size + 3 * n > S) {
+            while (top > 0) {
+                const int n = min(32, top);
+                if (top + 3 * n > S) {
                     // keep room for up to 4n children (an instance root has
-                    // four): hand the oldest entries to the next pass. After
-                    // it, size <= max(n, S/2) and size + 3n <= S for S >= 256.
-                    const int k = min(size - n, S / 2);
+                    // four): hand the oldest entries to the next pass and
+                    // move the rest down. Afterwards top <= max(n, S/2), so
+                    // top + 3n <= S for S >= 256.
+                    const int k = min(top - n, S / 2);
                     if (lane == 0)
                         atomicAdd(&a.ctrl->spills, 1ull);
-                    hand_back_stack<W, S>(a, out, stk, bot, k, inst0, lane);
-                    bot += k;
-                    __syncwarp();
+                    hand_back_stack<W, S>(a, out, stk, 0, k, inst0, lane);
+                    for (int j0 = 0; j0 < top - k; j0 += 32) {
+                        const int j = j0 + lane;
+                        const bool ok = j < top - k;
+                        B bb = 0;
+                        uint32_t mm = 0, oo = 0;
+                        if (ok)
+                            stk.get(k + j, bb, mm, oo);
+                        __syncwarp();
+                        if (ok)
+                            stk.put(j, bb, mm, oo);
+                        __syncwarp();
+                    }
+                    top -= k;
                 }
                 const bool act = lane < n;
                 B b = 0;
                 uint32_t mt = 0, org = 0;
                 if (act)
-                    stk.get((top - n + lane) & (S - 1), b, mt, org);
+                    stk.get(top - n + lane, b, mt, org);
                 top -= n;
                 nodes += (unsigned long long)n;
                 __syncwarp();
@@ -557,30 +599,31 @@ __global__ void k_search(const Dev<W> a)
                         atomicMin(&a.cnt.goal_origin[inst0], o);
                     }
                 }
-                const int p = (int)(mt & 31u);
-                const int s = (int)((mt >> 9) & 255u);
-                const unsigned allowed = (act && !goal) ? (LegalMoves<W>::at(p) & ~((mt >> 5) & 15u)) : 0u;
+                const uint32_t sh_p = mt & 127u;
+                const int s = (int)((mt >> 11) & 255u);
+                const unsigned allowed = (act && !goal) ? (LegalMoves<W>::at_sh(sh_p) & ~((mt >> 7) & 15u)) : 0u;
                 const bool low = s < 2;
-                const uint32_t sbase = (uint32_t)s << 9;
-                const LutRow<W> row = SharedLut<W>::row(lut, p);
+                const uint32_t sbase = mt & (255u << 11);
+                const LutRow<W> row = lut_row_sh<W>(lut, sh_p);
                 bool pruned = false;
                 int base = top;
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
                     const bool legal = (allowed >> m) & 1u;
-                    const int np = legal ? p + move_off<W>(m) : p;
-                    const unsigned t = tile_at<W>(b, np);
+                    // field offset of the tile that slides into the blank
+                    const uint32_t sh_np = sh_p + (uint32_t)(BITS * move_off<W>(m));
+                    const unsigned t = BoardOps<W>::tile(b, sh_np);
                     // h changes by +1 (away from the tile's goal cell) or -1
                     // and g by +1, so the child's slack is s - 2 or s
                     const bool away = away_bit<W>(row, m, t);
                     const bool push = legal && !(away && low);
                     pruned |= legal && away && low;
-                    const int q = legal ? p + move_low<W>(m) : 0;
-                    const B child = b ^ ((B)(t * move_mul<W>(m)) << (BITS * q));
-                    const uint32_t cm = ((uint32_t)np | ((1u << (3 - m)) << 5) | sbase) - (away ? (2u << 9) : 0u);
+                    const uint32_t sh_q = (m < 2) ? sh_np : sh_p;  // lower of the two fields
+                    const B child = BoardOps<W>::flip(b, t * move_mul<W>(m), sh_q);
+                    const uint32_t cm = (sh_np + sbase + ((1u << (3 - m)) << 7)) - (away ? (2u << 11) : 0u);
                     const unsigned pm = __ballot_sync(FULL, push);
                     if (push)
-                        stk.put((base + __popc(pm & lt)) & (S - 1), child, cm, org);
+                        stk.put(base + __popc(pm & lt), child, cm, org);
                     base += __popc(pm);
                 }
                 top = base;
@@ -608,7 +651,7 @@ __global__ void k_search(const Dev<W> a)
                     atomicMin(&a.cnt.fnext_off[inst0], fmin);
             }
             if (stop) {
-                hand_back_stack<W, S>(a, out, stk, bot, top - bot, inst0, lane);
+                hand_back_stack<W, S>(a, out, stk, 0, top, inst0, lane);
                 hand_back_records<W>(a, in, out, i + cnt, end, lane);
                 break;
             }
@@ -619,8 +662,7 @@ __global__ void k_search(const Dev<W> a)
     }
     if (!stop && lane == 0)
         atomicAdd(&a.ctrl->exited, 1);
-    __syncthreads();
-    if (threadIdx.x == 0)
+    if (lane == 0)
         atomicMax(&a.ctrl->t_end, global_ns());
 }
 
