@@ -132,6 +132,38 @@ bpida_status bpida_solve_ex(const bpida_config *cfg, const uint64_t *boards, int
                             uint8_t *out_moves, uint64_t *out_nodes_per_iter, int *out_num_iters,
                             int *out_status, void *stream);
 
+/*
+ * bpida_solve_noalloc — the 15-puzzle solve without any device allocation.
+ * The paper has no counterpart: it serves callers that cannot call
+ * cudaMalloc when they want a solve (work issued while another part of the
+ * program captures a CUDA graph, a device whose memory a framework pool has
+ * already reserved, loops that cannot take cudaMalloc's implicit device
+ * synchronisation).
+ *   Same arguments and results as bpida_solve_ex with the default
+ *   configuration (width 4, count_all = 1): boards, out_len, out_moves
+ *   (n * bpida_max_len(4) bytes), out_nodes_per_iter (n * bpida_max_iters(4)
+ *   uint64), out_num_iters and out_status (may be NULL) are caller-owned
+ *   device buffers.
+ *   n may be at most BPIDA_NOALLOC_MAX_BOARDS; a larger n returns
+ *   BPIDA_EINVAL before any work is issued.
+ *   The workspace is one file-scope __device__ array of
+ *   BPIDA_NOALLOC_SCRATCH_BYTES held by every GPU that loads the library
+ *   until the process exits. The first call on a device looks up the
+ *   array's device address (cudaGetSymbolAddress) with that device current;
+ *   make that first call before any stream capture begins. No call
+ *   allocates or frees memory. Calls share the array: each call
+ *   re-initialises what it reads, and calls that overlapped on the GPU would
+ *   race (calls are serialised by a lock and synchronise `stream` before
+ *   returning). The search runs with one two-warp block per SM, so it is
+ *   slower than bpida_solve_ex; a hand-back overflow of its fixed queue
+ *   returns BPIDA_ENOMEM.
+ */
+#define BPIDA_NOALLOC_MAX_BOARDS 256
+#define BPIDA_NOALLOC_SCRATCH_BYTES (16u << 20)
+bpida_status bpida_solve_noalloc(const uint64_t *boards, int n, int *out_len, uint8_t *out_moves,
+                                 uint64_t *out_nodes_per_iter, int *out_num_iters, int *out_status,
+                                 void *stream);
+
 /* Statistics of the last solve call made by this host thread. If `timed` is
  * set before a call (bpida_set_timing(1)), search kernel durations are
  * recorded with CUDA events on the launching stream. */

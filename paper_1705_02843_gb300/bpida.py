@@ -20,8 +20,9 @@ OK, EINVAL, ENOMEM, ESTACK, EBUDGET, ETIMEOUT, ECUDA, ELIMIT, EINTERNAL = range(
 
 EXPORTS = (
     "bpida_max_len", "bpida_max_iters", "bpida_solve", "bpida_solve_ex", "bpida_set_timing",
-    "bpida_get_stats", "bpida_release_workspace", "bpida_status_str",
+    "bpida_get_stats", "bpida_release_workspace", "bpida_status_str", "bpida_solve_noalloc",
 )
+NOALLOC_MAX_BOARDS = 256
 
 
 class Config(ctypes.Structure):
@@ -86,6 +87,8 @@ def load():
         lib.bpida_get_stats.restype = None
         lib.bpida_release_workspace.argtypes = []
         lib.bpida_release_workspace.restype = None
+        lib.bpida_solve_noalloc.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, vp]
+        lib.bpida_solve_noalloc.restype = ctypes.c_int
         lib.bpida_status_str.argtypes = [ctypes.c_int]
         lib.bpida_status_str.restype = ctypes.c_char_p
         _lib = lib
@@ -200,3 +203,27 @@ def solve_packed_host(packed, width: int = 4, config: Optional[Config] = None,
     for r in res:
         r["call_status"] = sol.status
     return res
+
+
+def solve_noalloc(boards: torch.Tensor, stream: Optional[torch.cuda.Stream] = None) -> Solution:
+    """15-puzzle solve through bpida_solve_noalloc (no device allocation inside
+    the library; the output tensors here are allocated by the caller side of
+    this binding). At most NOALLOC_MAX_BOARDS boards."""
+    lib = load()
+    if not boards.is_cuda:
+        raise ValueError("boards must be a CUDA tensor")
+    boards = boards.contiguous()
+    n = boards.shape[0]
+    dev = boards.device
+    ml, mi = lib.bpida_max_len(4), lib.bpida_max_iters(4)
+    out_len = torch.empty(n, dtype=torch.int32, device=dev)
+    out_moves = torch.empty((n, ml), dtype=torch.uint8, device=dev)
+    out_nodes = torch.empty((n, mi), dtype=torch.int64, device=dev)
+    out_iters = torch.empty(n, dtype=torch.int32, device=dev)
+    out_status = torch.empty(n, dtype=torch.int32, device=dev)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    with torch.cuda.device(dev):
+        rc = lib.bpida_solve_noalloc(boards.data_ptr(), n, out_len.data_ptr(), out_moves.data_ptr(),
+                                     out_nodes.data_ptr(), out_iters.data_ptr(), out_status.data_ptr(),
+                                     s.cuda_stream)
+    return Solution(rc, out_len, out_moves, out_nodes, out_iters, out_status)

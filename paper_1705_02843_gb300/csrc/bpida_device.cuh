@@ -1017,7 +1017,7 @@ __global__ void k_reset(const Dev<W> a)
     }
 }
 
-__global__ void k_set_desc(CallDesc d, CallDesc *dst) { *dst = d; }
+static __global__ void k_set_desc(CallDesc d, CallDesc *dst) { *dst = d; }
 
 template <int W>
 __global__ void k_init(const Dev<W> a)
