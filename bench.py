@@ -172,6 +172,56 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args):
+    """Continuous batching under Poisson arrivals (98% walks of 30-90 moves,
+    2% random permutations): completed requests/s and p50/p99 latency from
+    submit to pollable result, per arrival rate."""
+    import torch
+
+    from paper_1705_02843_gb300 import bpida
+
+    torch.cuda.set_device(0)
+    rates = [float(r) for r in args.serving_rates.split(",")]
+    out = []
+    for rate in rates:
+        n_req = int(min(args.serving_max_requests, rate * args.serving_seconds))
+        stream = I.serving_stream(rate, n_req, seed=300000 + int(rate))
+        words = [int(w) for w in I.packed_array([x for _, x in stream])]
+        lat, t_first, t_last = [], None, None
+        with bpida.Server(frontier_bytes=2 << 30, max_slots=8192) as sv:
+            t0 = bpida.Server.clock()
+            i = 0
+            got = 0
+            while got < n_req:
+                now = bpida.Server.clock() - t0
+                while i < n_req and stream[i][0] <= now:
+                    sv.submit(words[i], i)
+                    i += 1
+                for r in sv.poll():
+                    if r["status"] != 0:
+                        raise RuntimeError("request %d failed: %s" % (r["req_id"], bpida.status_str(r["status"])))
+                    lat.append(r["latency_s"])
+                    got += 1
+                if i < n_req:
+                    wait = stream[i][0] - (bpida.Server.clock() - t0)
+                    if wait > 0.0005:
+                        time.sleep(min(wait, 0.002))
+                else:
+                    time.sleep(0.0005)
+            t_end = bpida.Server.clock() - t0
+            st = sv.stats()
+        lat.sort()
+        out.append({"rate_per_s": rate, "requests": n_req, "completed_per_s": n_req / t_end,
+                    "p50_ms": 1e3 * lat[len(lat) // 2], "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                    "device_steps": st["steps"], "max_active": st["max_active"], "wall_s": t_end})
+        print(json.dumps(out[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "15-puzzle serving: completed requests/s and p50/p99 latency (submit to result)",
+                      "unit": "requests/s", "data": "synthetic",
+                      "config": {"workload": "Poisson arrivals; 98% walks of 30-90 moves, 2% random permutations",
+                                 "slots": 8192, "mode": "continuous batching"},
+                      "rates": out}), flush=True)
+
+
 def pick_cpu_sample(insts, gold, budget_nodes):
     cores = os.cpu_count() or 1
     if gold:
@@ -196,6 +246,11 @@ def main():
     ap.add_argument("--workload", default="perms15_100", choices=["perms15_100"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-nodes", type=float, default=1.5e9)
+    ap.add_argument("--serving", action="store_true",
+                    help="run the continuous-batching service under Poisson arrivals instead")
+    ap.add_argument("--serving-rates", default="1000,2000,5000,10000,20000,50000")
+    ap.add_argument("--serving-seconds", type=float, default=2.0)
+    ap.add_argument("--serving-max-requests", type=int, default=20000)
     ap.add_argument("--driver", default="graph", choices=["graph", "host"],
                     help="graph: each solve call is one CUDA graph launch (default); host: the "
                          "host launches every kernel (same kernels; ncu can list them)")
@@ -209,6 +264,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.serving:
+        run_serving(args)
         return
 
     import torch

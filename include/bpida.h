@@ -80,7 +80,8 @@ typedef struct {
                              1 = the host launches every kernel and reads
                              the loop state back after every search pass
                              (needed for per-launch CUDA-event timing) */
-    int reserved;
+    int min_pass_us;      /* a pass hands work back only after running this
+                             long (microseconds); 0 = auto, -1 = no minimum */
 } bpida_config;
 
 typedef struct {
@@ -163,6 +164,58 @@ bpida_status bpida_solve_ex(const bpida_config *cfg, const uint64_t *boards, int
 bpida_status bpida_solve_noalloc(const uint64_t *boards, int n, int *out_len, uint8_t *out_moves,
                                  uint64_t *out_nodes_per_iter, int *out_num_iters, int *out_status,
                                  void *stream);
+
+/*
+ * Serving: a continuous-batching solve service for the 15-puzzle (the
+ * paper solves one instance per run; this is the batched solver kept
+ * running). Requests are submitted one board at a time from host memory at
+ * any moment; a background host thread admits them into free instance slots
+ * between threshold steps, so newly arrived requests share every search
+ * pass with those already on the GPU, each with its own f-limit. Search
+ * state stays in device memory across thresholds. Results (the same as
+ * bpida_solve_ex gives for that board alone: all-solutions node counts, the
+ * lexicographically first optimal solution) are posted to a completion
+ * queue as soon as the request finishes.
+ */
+typedef struct bpida_server bpida_server;
+
+typedef struct {
+    uint64_t req_id;
+    int status;                 /* bpida_status of the request */
+    int length;                 /* optimal length, -1 if none */
+    int num_iters;              /* iterations run */
+    int pad;
+    double submit_time_s;       /* bpida_server_clock() at submit */
+    double done_time_s;         /* bpida_server_clock() when it became pollable */
+    uint8_t moves[80];          /* first optimal solution, zero-filled */
+    uint64_t nodes_per_iter[41];/* nodes expanded per iteration, zero-filled */
+} bpida_result;
+
+typedef struct {
+    int slots;                  /* instance slots (bounded by frontier memory) */
+    int max_active;             /* most instances searched in one step */
+    uint64_t submitted, admitted, completed;
+    uint64_t steps, passes;     /* device threshold steps and search passes */
+} bpida_server_stats;
+
+/* Create a server on the current device. cfg may be NULL (width must be 4;
+ * split_target, exit_fraction_pct and min_rounds are honoured). The number
+ * of slots is min(max_slots, frontier_bytes / (48 * (4*split_target + 4)))
+ * (split_target 0 means 256): each slot owns its frontier records.
+ * Returns NULL on failure. */
+bpida_server *bpida_server_create(const bpida_config *cfg, size_t frontier_bytes, int max_slots);
+/* Queue one request: host_board points to one packed 15-puzzle word (host
+ * memory, read before returning). Thread-safe, non-blocking. */
+bpida_status bpida_server_submit(bpida_server *sv, const uint64_t *host_board, uint64_t req_id);
+/* Move up to max finished results into out; returns how many. Non-blocking. */
+int bpida_server_poll(bpida_server *sv, bpida_result *out, int max);
+/* Requests submitted and not yet finished. */
+int bpida_server_in_flight(bpida_server *sv);
+void bpida_server_get_stats(bpida_server *sv, bpida_server_stats *out);
+/* The clock used for submit_time_s / done_time_s (seconds, monotonic). */
+double bpida_server_clock(void);
+/* Stop the service (pending requests are dropped) and free it. */
+void bpida_server_destroy(bpida_server *sv);
 
 /* Statistics of the last solve call made by this host thread. If `timed` is
  * set before a call (bpida_set_timing(1)), search kernel durations are

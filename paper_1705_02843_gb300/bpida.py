@@ -21,6 +21,8 @@ OK, EINVAL, ENOMEM, ESTACK, EBUDGET, ETIMEOUT, ECUDA, ELIMIT, EINTERNAL = range(
 EXPORTS = (
     "bpida_max_len", "bpida_max_iters", "bpida_solve", "bpida_solve_ex", "bpida_set_timing",
     "bpida_get_stats", "bpida_release_workspace", "bpida_status_str", "bpida_solve_noalloc",
+    "bpida_server_create", "bpida_server_submit", "bpida_server_poll", "bpida_server_in_flight",
+    "bpida_server_get_stats", "bpida_server_clock", "bpida_server_destroy",
 )
 NOALLOC_MAX_BOARDS = 256
 
@@ -36,7 +38,7 @@ class Config(ctypes.Structure):
         ("min_rounds", ctypes.c_int),
         ("node_budget", ctypes.c_uint64),
         ("driver", ctypes.c_int),
-        ("reserved", ctypes.c_int),
+        ("min_pass_us", ctypes.c_int),
     ]
 
 
@@ -55,6 +57,42 @@ class Stats(ctypes.Structure):
         ("spills", ctypes.c_uint64),
         ("max_handed_back", ctypes.c_int),
         ("search_ms_device", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Result(ctypes.Structure):
+    _fields_ = [
+        ("req_id", ctypes.c_uint64),
+        ("status", ctypes.c_int),
+        ("length", ctypes.c_int),
+        ("num_iters", ctypes.c_int),
+        ("pad", ctypes.c_int),
+        ("submit_time_s", ctypes.c_double),
+        ("done_time_s", ctypes.c_double),
+        ("moves", ctypes.c_uint8 * 80),
+        ("nodes_per_iter", ctypes.c_uint64 * 41),
+    ]
+
+    def as_dict(self):
+        L = self.length
+        return {"req_id": self.req_id, "status": self.status, "length": L,
+                "moves": list(self.moves[:max(L, 0)]), "iters": self.num_iters,
+                "nodes": list(self.nodes_per_iter[:self.num_iters]),
+                "latency_s": self.done_time_s - self.submit_time_s}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [
+        ("slots", ctypes.c_int),
+        ("max_active", ctypes.c_int),
+        ("submitted", ctypes.c_uint64),
+        ("admitted", ctypes.c_uint64),
+        ("completed", ctypes.c_uint64),
+        ("steps", ctypes.c_uint64),
+        ("passes", ctypes.c_uint64),
     ]
 
     def as_dict(self):
@@ -89,6 +127,20 @@ def load():
         lib.bpida_release_workspace.restype = None
         lib.bpida_solve_noalloc.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, vp]
         lib.bpida_solve_noalloc.restype = ctypes.c_int
+        lib.bpida_server_create.argtypes = [ctypes.POINTER(Config), ctypes.c_size_t, ctypes.c_int]
+        lib.bpida_server_create.restype = vp
+        lib.bpida_server_submit.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint64]
+        lib.bpida_server_submit.restype = ctypes.c_int
+        lib.bpida_server_poll.argtypes = [vp, ctypes.POINTER(Result), ctypes.c_int]
+        lib.bpida_server_poll.restype = ctypes.c_int
+        lib.bpida_server_in_flight.argtypes = [vp]
+        lib.bpida_server_in_flight.restype = ctypes.c_int
+        lib.bpida_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        lib.bpida_server_get_stats.restype = None
+        lib.bpida_server_clock.argtypes = []
+        lib.bpida_server_clock.restype = ctypes.c_double
+        lib.bpida_server_destroy.argtypes = [vp]
+        lib.bpida_server_destroy.restype = None
         lib.bpida_status_str.argtypes = [ctypes.c_int]
         lib.bpida_status_str.restype = ctypes.c_char_p
         _lib = lib
@@ -150,9 +202,9 @@ class Solution:
 
 def make_config(width: int = 4, split_target: int = 0, warps_per_block: int = 0,
                 stack_entries: int = 0, exit_fraction_pct: int = 0, min_rounds: int = 0,
-                node_budget: int = 0, driver: int = 0) -> Config:
+                node_budget: int = 0, driver: int = 0, min_pass_us: int = 0) -> Config:
     return Config(width, 1, split_target, warps_per_block, stack_entries, exit_fraction_pct,
-                  min_rounds, node_budget, driver, 0)
+                  min_rounds, node_budget, driver, min_pass_us)
 
 
 def solve(boards: torch.Tensor, width: int = 4, config: Optional[Config] = None,
@@ -227,3 +279,54 @@ def solve_noalloc(boards: torch.Tensor, stream: Optional[torch.cuda.Stream] = No
                                      out_nodes.data_ptr(), out_iters.data_ptr(), out_status.data_ptr(),
                                      s.cuda_stream)
     return Solution(rc, out_len, out_moves, out_nodes, out_iters, out_status)
+
+
+class Server:
+    """Continuous-batching 15-puzzle solve service (bpida_server_* calls)."""
+
+    def __init__(self, frontier_bytes: int = 1 << 30, max_slots: int = 4096,
+                 config: Optional[Config] = None):
+        lib = load()
+        cfg = config if config is not None else make_config(4)
+        self._lib = lib
+        self._h = lib.bpida_server_create(ctypes.byref(cfg), frontier_bytes, max_slots)
+        if not self._h:
+            raise RuntimeError("bpida_server_create failed")
+        self._buf = (Result * 256)()
+
+    def submit(self, packed_board: int, req_id: int) -> None:
+        w = ctypes.c_uint64(packed_board)
+        rc = self._lib.bpida_server_submit(self._h, ctypes.byref(w), req_id)
+        if rc != OK:
+            raise RuntimeError("submit failed: " + status_str(rc))
+
+    def poll(self) -> List[dict]:
+        out = []
+        while True:
+            k = self._lib.bpida_server_poll(self._h, self._buf, len(self._buf))
+            out.extend(self._buf[i].as_dict() for i in range(k))
+            if k < len(self._buf):
+                return out
+
+    def in_flight(self) -> int:
+        return self._lib.bpida_server_in_flight(self._h)
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        self._lib.bpida_server_get_stats(self._h, ctypes.byref(s))
+        return s.as_dict()
+
+    @staticmethod
+    def clock() -> float:
+        return load().bpida_server_clock()
+
+    def close(self) -> None:
+        if self._h:
+            self._lib.bpida_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

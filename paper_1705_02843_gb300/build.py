@@ -7,7 +7,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libbpida.so")
-SOURCES = [os.path.join(HERE, "csrc", "bpida.cu"), os.path.join(HERE, "csrc", "bpida_noalloc.cu")]
+SOURCES = [os.path.join(HERE, "csrc", n) for n in ("bpida.cu", "bpida_noalloc.cu", "bpida_server.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", "bpida_device.cuh"), os.path.join(ROOT, "include", "bpida.h")]
 
 NVCC_FLAGS = [

@@ -3,19 +3,20 @@
 //
 // One solve call runs all of its instances together. Every step closes one
 // f-limited iteration of every still-active instance (each at its own
-// limit): k_split builds each instance's root set, k_scan/k_compact gather
-// the root sets into one queue, k_search passes consume the queue with
-// persistent warps (another pass only when warps handed work back), and
-// k_advance records the iteration's node count and raises each limit to the
-// smallest pruned f (or, once a goal was popped, walks down the first
-// goal-bearing root to recover the solution path).
+// limit): k_split builds each instance's root set (its last block computes
+// the frontier offsets), k_search passes consume the frontiers with
+// persistent warps (another pass only when warps handed work back; the last
+// warp of a pass decides), and k_advance records the iteration's node count
+// and raises each limit to the smallest pruned f, or, once a goal was
+// popped, walks down the first goal-bearing root to recover the solution
+// path (its last block closes the step).
 //
 // By default the whole loop is one CUDA graph: the step loop and the pass
-// loop are conditional WHILE nodes whose conditions are set on the device
-// (k_step_end, k_pass_end), so a call is one graph launch and one final
-// synchronisation. The host-driven loop (driver = 1) launches the same
-// kernels one by one and reads the control block back after every pass; it
-// is what times each search launch with CUDA events.
+// loop are conditional WHILE nodes whose conditions are set on the device,
+// so a call is one graph launch and one final synchronisation. The
+// host-driven loop (driver = 1) launches the same kernels one by one and
+// reads the control block back after every pass; it is what times each
+// search launch with CUDA events.
 #include "bpida.h"
 #include "bpida_device.cuh"
 
@@ -41,8 +42,8 @@ struct DevBuf {
     size_t n = 0;
 };
 
-// W, S, warps per block, n, frontier cap, hand-back percentage, min rounds
-typedef std::tuple<int, int, int, int, int, int, int> PlanKey;
+// W, S, warps per block, n, frontier cap, hand-back percentage, min rounds, min pass time
+typedef std::tuple<int, int, int, int, int, int, int, int> PlanKey;
 
 struct Plan {
     cudaGraph_t graph = nullptr;
@@ -145,7 +146,7 @@ template <int W> MoveLut<W> make_lut()
 }
 
 struct Settings {
-    int width, count_all, split_target, wpb, S, exit_pct, min_rounds, driver;
+    int width, count_all, split_target, wpb, S, exit_pct, min_rounds, driver, min_pass_ns;
     uint64_t budget;
 };
 
@@ -193,9 +194,8 @@ struct Geometry {
     int n_cap;
 };
 
-// The whole solve as one graph:
-//   reset -> init -> begin -> WHILE(step){ split -> scan -> compact ->
-//   WHILE(pass){ search -> pass_end } -> advance -> step_end } -> finalize
+// The whole solve as one graph (k_set_desc is launched before it):
+//   init -> WHILE(step){ split -> WHILE(pass){ search } -> advance } -> finalize
 template <int W, int S>
 cudaError_t build_graph(Plan &pl, Dev<W> d, const Geometry &g)
 {
@@ -210,17 +210,13 @@ cudaError_t build_graph(Plan &pl, Dev<W> d, const Geometry &g)
     d.graph = 1;
     d.h_step = hs;
     d.h_pass = 0;
-    const dim3 one(1), b128(128), b256(256), b1024(1024);
+    const dim3 b128(128), bsplit(SPLIT_THREADS);
     const dim3 g_inst((g.n_cap + 127) / 128), g_prob(g.n_cap);
-    cudaGraphNode_t n_reset, n_init, n_begin, n_step, n_fin;
-    if ((e = add_kernel(&n_reset, G, nullptr, 0, k_reset<W>, one, one, 0, d)) != cudaSuccess)
-        return e;
-    if ((e = add_kernel(&n_init, G, &n_reset, 1, k_init<W>, g_inst, b128, 0, d)) != cudaSuccess)
-        return e;
-    if ((e = add_kernel(&n_begin, G, &n_init, 1, k_begin<W>, one, one, 0, d)) != cudaSuccess)
+    cudaGraphNode_t n_init, n_step, n_fin;
+    if ((e = add_kernel(&n_init, G, nullptr, 0, k_init<W>, g_inst, b128, 0, d)) != cudaSuccess)
         return e;
     cudaGraph_t B;
-    if ((e = add_while(&n_step, G, &n_begin, 1, hs, &B)) != cudaSuccess)
+    if ((e = add_while(&n_step, G, &n_init, 1, hs, &B)) != cudaSuccess)
         return e;
     if ((e = add_kernel(&n_fin, G, &n_step, 1, k_finalize<W>, g_inst, b128, 0, d)) != cudaSuccess)
         return e;
@@ -228,26 +224,18 @@ cudaError_t build_graph(Plan &pl, Dev<W> d, const Geometry &g)
     if ((e = cudaGraphConditionalHandleCreate(&hp, B, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
         return e;
     d.h_pass = hp;
-    cudaGraphNode_t n_split, n_scan, n_compact, n_pass, n_adv, n_send;
-    if ((e = add_kernel(&n_split, B, nullptr, 0, k_split<W>, g_prob, b256, 0, d)) != cudaSuccess)
-        return e;
-    if ((e = add_kernel(&n_scan, B, &n_split, 1, k_scan<W>, one, b1024, 0, d)) != cudaSuccess)
-        return e;
-    if ((e = add_kernel(&n_compact, B, &n_scan, 1, k_compact<W>, g_prob, b128, 0, d)) != cudaSuccess)
+    cudaGraphNode_t n_split, n_pass, n_adv;
+    if ((e = add_kernel(&n_split, B, nullptr, 0, k_split<W>, g_prob, bsplit, 0, d)) != cudaSuccess)
         return e;
     cudaGraph_t P;
-    if ((e = add_while(&n_pass, B, &n_compact, 1, hp, &P)) != cudaSuccess)
+    if ((e = add_while(&n_pass, B, &n_split, 1, hp, &P)) != cudaSuccess)
         return e;
     if ((e = add_kernel(&n_adv, B, &n_pass, 1, k_advance<W>, g_inst, b128, 0, d)) != cudaSuccess)
         return e;
-    if ((e = add_kernel(&n_send, B, &n_adv, 1, k_step_end<W>, one, one, 0, d)) != cudaSuccess)
-        return e;
 
-    cudaGraphNode_t n_search, n_pend;
+    cudaGraphNode_t n_search;
     if ((e = add_kernel(&n_search, P, nullptr, 0, k_search<W, S>, dim3(g.grid), dim3(g.threads), g.smem, d)) !=
         cudaSuccess)
-        return e;
-    if ((e = add_kernel(&n_pend, P, &n_search, 1, k_pass_end<W>, one, one, 0, d)) != cudaSuccess)
         return e;
     return cudaGraphInstantiate(&pl.exec, G, 0);
 }
@@ -266,9 +254,13 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     g.n_cap = n;
     g.threads = cfg.wpb * 32;
     g.smem = SharedLut<W>::BYTES + (size_t)cfg.wpb * S * WarpStack<W>::ENTRY_BYTES;
-    CK(cudaFuncSetAttribute(k_search<W, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem));
-    int bpsm = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_search<W, S>, g.threads, g.smem));
+    // blocks of k_search per SM, looked up once per (device, W, S, block size)
+    static std::map<std::tuple<int, int>, int> occ;
+    int &bpsm = occ[std::make_tuple(dev, cfg.wpb)];
+    if (bpsm == 0) {
+        CK(cudaFuncSetAttribute(k_search<W, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_search<W, S>, g.threads, g.smem));
+    }
     if (bpsm < 1)
         return BPIDA_EINVAL;
     g.grid = sms * bpsm;
@@ -332,6 +324,7 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     d.tune.target_cap = g.tcap;
     d.tune.target_path = std::min(g.tcap, 4096);
     d.tune.growth = 8;
+    d.tune.min_pass_ns = cfg.min_pass_ns;
     d.lut = make_lut<W>();
 
     CallDesc desc;
@@ -344,7 +337,7 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     desc.out_status = out_status;
     desc.node_budget = cfg.budget;
     desc.n = n;
-    k_set_desc<<<1, 1, 0, st>>>(desc, (CallDesc *)ws.desc.p);
+    k_set_desc<<<1, 1, 0, st>>>(desc, (CallDesc *)ws.desc.p, d.ctrl);
     CK(cudaGetLastError());
 
     bpida_stats stats;
@@ -353,10 +346,10 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     stats.block_threads = g.threads;
     stats.sm_count = sms;
 
-    const dim3 one(1), b128(128), b256(256), b1024(1024);
+    const dim3 b128(128), bsplit(SPLIT_THREADS);
     const dim3 g_inst((n + 127) / 128);
     if (cfg.driver == 0) {
-        const PlanKey key(W, S, cfg.wpb, n, g.tcap, cfg.exit_pct, cfg.min_rounds);
+        const PlanKey key(W, S, cfg.wpb, n, g.tcap, cfg.exit_pct, cfg.min_rounds, cfg.min_pass_ns);
         Plan &pl = ws.plans[key];
         if (pl.exec && pl.gen != ws.gen)
             pl.destroy();
@@ -372,23 +365,20 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
         CK(cudaGraphLaunch(pl.exec, st));
         CK(cudaMemcpyAsync(ws.h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        stats.launches = 1 + 4 + 5 * ws.h_ctrl->steps + 2 * (int)ws.h_ctrl->passes_total;
+        stats.launches = 3 + 2 * ws.h_ctrl->steps + (int)ws.h_ctrl->passes_total;
     } else {
         // host-driven loop over the same kernels
         d.graph = 0;
-        k_reset<W><<<1, 1, 0, st>>>(d);
         k_init<W><<<g_inst, b128, 0, st>>>(d);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(ws.h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        stats.launches = 3;
+        stats.launches = 2;
         int n_active = ws.h_ctrl->n_active;
         while (n_active > 0) {
-            k_split<W><<<n_active, b256, 0, st>>>(d);
-            k_scan<W><<<1, b1024, 0, st>>>(d);
-            k_compact<W><<<n_active, b128, 0, st>>>(d);
+            k_split<W><<<n_active, bsplit, 0, st>>>(d);
             CK(cudaGetLastError());
-            stats.launches += 3;
+            stats.launches += 1;
             for (;;) {
                 if (g_timing)
                     CK(cudaEventRecord(ws.ev0, st));
@@ -396,9 +386,7 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
                 CK(cudaGetLastError());
                 if (g_timing)
                     CK(cudaEventRecord(ws.ev1, st));
-                k_pass_end<W><<<1, 1, 0, st>>>(d);
-                CK(cudaGetLastError());
-                stats.launches += 2;
+                stats.launches += 1;
                 CK(cudaMemcpyAsync(ws.h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
                 CK(cudaStreamSynchronize(st));
                 if (g_timing) {
@@ -410,9 +398,8 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
                     break;
             }
             k_advance<W><<<(n_active + 127) / 128, b128, 0, st>>>(d);
-            k_step_end<W><<<1, 1, 0, st>>>(d);
             CK(cudaGetLastError());
-            stats.launches += 2;
+            stats.launches += 1;
             CK(cudaMemcpyAsync(ws.h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             n_active = ws.h_ctrl->step_again ? ws.h_ctrl->n_active : 0;
@@ -490,6 +477,8 @@ bpida_status bpida_solve_ex(const bpida_config *cfg_in, const uint64_t *boards, 
     cfg.exit_pct = (cfg_in && cfg_in->exit_fraction_pct > 0) ? cfg_in->exit_fraction_pct : 10;
     cfg.min_rounds = (cfg_in && cfg_in->min_rounds > 0) ? cfg_in->min_rounds : 64;
     cfg.driver = cfg_in ? cfg_in->driver : 0;
+    cfg.min_pass_ns = (cfg_in && cfg_in->min_pass_us != 0) ? (cfg_in->min_pass_us < 0 ? 0 : cfg_in->min_pass_us * 1000)
+                                                             : 10000;
     cfg.budget = cfg_in ? cfg_in->node_budget : 0;
     if (cfg.width < 3 || cfg.width > 5 || n < 0)
         return BPIDA_EINVAL;

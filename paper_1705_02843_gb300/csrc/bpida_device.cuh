@@ -162,8 +162,12 @@ struct Ctrl {
     int steps;        // threshold steps completed
     int passes_step;  // search passes in this step
     int max_out;      // largest hand-back of one pass
-    int pass_again;   // set by k_pass_end: another pass follows
-    int step_again;   // set by k_step_end: another step follows
+    int pass_again;   // set at the end of a pass: another pass follows
+    int step_again;   // set at the end of a step: another step follows
+    int first_pass;   // 1: this pass reads the splitter's frontiers in place
+    int done_warps;   // search warps finished in this pass
+    int done_blocks;  // blocks finished in the current split / advance / init
+    int n_done;       // serving: entries of the done list
     unsigned long long records_total;
     unsigned long long handed_back_total;
     unsigned long long search_nodes_total;  // nodes popped by k_search
@@ -227,6 +231,7 @@ struct Tune {
     int target_cap;      // per-problem frontier cap
     int target_path;     // frontier records wanted for a path step
     int growth;          // expected node growth per iteration (x)
+    int min_pass_ns;     // a pass hands work back only after running this long
 };
 
 // ---------------------------------------------------------------------
@@ -300,6 +305,7 @@ template <int W> struct Dev {
     MoveLut<W> lut;
     cudaGraphConditionalHandle h_step, h_pass;
     int graph;                  // 1 inside the CUDA graph (sets the loop conditions)
+    unsigned *done_list;        // serving: instances that finished in this step (else null)
 };
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -477,9 +483,31 @@ __device__ __forceinline__ void hand_back_stack(const Dev<W> &a, Rec<W> *out, co
     }
 }
 
+// Input record idx of a pass. The first pass of a step reads the splitter's
+// per-problem frontiers in place: problem k owns indices
+// [offset[k], offset[k] + count[k]); the origin of a frontier record is its
+// index. Later passes read the hand-back queue.
 template <int W>
-__device__ __forceinline__ void hand_back_records(const Dev<W> &a, const Rec<W> *in, Rec<W> *out, int from,
-                                                  int to, int lane)
+__device__ __forceinline__ Rec<W> load_rec(const Dev<W> &a, bool frontier, int n_active, const Rec<W> *in, int idx)
+{
+    if (!frontier)
+        return in[idx];
+    int lo = 0, hi = n_active - 1;  // last k with offset[k] <= idx
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.offset[mid] <= idx)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    Rec<W> r = a.scratch[(size_t)lo * 2 * a.C + (idx - a.offset[lo])];
+    r.origin = (uint32_t)idx;
+    return r;
+}
+
+template <int W>
+__device__ __forceinline__ void hand_back_records(const Dev<W> &a, bool frontier, int n_active, const Rec<W> *in,
+                                                  Rec<W> *out, int from, int to, int lane)
 {
     const int k = to - from;
     if (k <= 0)
@@ -494,8 +522,10 @@ __device__ __forceinline__ void hand_back_records(const Dev<W> &a, const Rec<W> 
         return;
     }
     for (int j = lane; j < k; j += 32)
-        out[base + j] = in[from + j];
+        out[base + j] = load_rec<W>(a, frontier, n_active, in, from + j);
 }
+
+template <int W> __device__ void end_of_pass(const Dev<W> &a);
 
 // One warp = one shared stack (Algorithm 1's openList). Each round pops up
 // to 32 nodes (one per lane), tests them for the goal, and generates the
@@ -517,6 +547,8 @@ __global__ void k_search(const Dev<W> a)
     __syncthreads();
     const Rec<W> *in = a.ctrl->qi ? a.q1 : a.q0;
     Rec<W> *out = a.ctrl->qi ? a.q0 : a.q1;
+    const bool frontier = a.ctrl->first_pass != 0;
+    const int n_act = a.ctrl->n_active;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpStack<W> stk;
@@ -544,7 +576,7 @@ __global__ void k_search(const Dev<W> a)
             const bool v = idx < end;
             Rec<W> r;
             if (v)
-                r = in[idx];
+                r = load_rec<W>(a, frontier, n_act, in, idx);
             const unsigned inst = v ? r.inst : 0xffffffffu;
             const unsigned inst0 = __shfl_sync(FULL, inst, 0);
             const unsigned same = __ballot_sync(FULL, v && inst == inst0);
@@ -632,11 +664,13 @@ __global__ void k_search(const Dev<W> a)
                 __syncwarp();
 
                 if (((++rounds) & 31) == 0 && rounds >= a.tune.min_rounds) {
-                    int ex = 0;
-                    if (lane == 0)
-                        ex = *(volatile int *)&a.ctrl->exited;
-                    ex = __shfl_sync(FULL, ex, 0);
-                    if (ex >= a.tune.exit_threshold) {
+                    // hand back once enough warps have run dry and the pass
+                    // has run long enough to pay for another one
+                    int go = 0;
+                    if (lane == 0 && *(volatile int *)&a.ctrl->exited >= a.tune.exit_threshold)
+                        go = global_ns() - *(volatile unsigned long long *)&a.ctrl->t_start >=
+                             (unsigned long long)a.tune.min_pass_ns;
+                    if (__shfl_sync(FULL, go, 0)) {
                         stop = true;
                         break;
                     }
@@ -652,7 +686,7 @@ __global__ void k_search(const Dev<W> a)
             }
             if (stop) {
                 hand_back_stack<W, S>(a, out, stk, 0, top, inst0, lane);
-                hand_back_records<W>(a, in, out, i + cnt, end, lane);
+                hand_back_records<W>(a, frontier, n_act, in, out, i + cnt, end, lane);
                 break;
             }
             i += cnt;
@@ -662,8 +696,17 @@ __global__ void k_search(const Dev<W> a)
     }
     if (!stop && lane == 0)
         atomicAdd(&a.ctrl->exited, 1);
-    if (lane == 0)
+    // the last warp to finish closes the pass
+    int last = 0;
+    if (lane == 0) {
         atomicMax(&a.ctrl->t_end, global_ns());
+        __threadfence();
+        last = atomicAdd(&a.ctrl->done_warps, 1) == total_warps - 1;
+    }
+    if (__shfl_sync(FULL, last, 0) && lane == 0) {
+        __threadfence();
+        end_of_pass<W>(a);
+    }
 }
 
 // ---------------------------------------------------------------------
@@ -671,199 +714,207 @@ __global__ void k_search(const Dev<W> a)
 // expansion of the problem's root until the level holds `target` records
 // (Algorithm 1's CreateRootSet, rebuilt every iteration). Nodes expanded
 // here are counted here; the final level becomes the problem's frontier.
+// Small levels stay in shared memory. The last block to finish computes the
+// frontier offsets (exclusive scan of the record counts) and opens the
+// step's first search pass, which reads the frontiers in place.
 // ---------------------------------------------------------------------
+template <int W> struct SplitShared {
+    static constexpr int CAP = (W <= 4) ? 512 : 384;  // records per shared level buffer
+};
+static constexpr int SPLIT_THREADS = 512;
+
 template <int W>
-__global__ void k_split(const Dev<W> a)
+__device__ __forceinline__ bool last_block_done(unsigned *counter, int *s_last)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(counter, 1u);
+        *s_last = (t == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (*s_last) {
+        __threadfence();
+        return true;
+    }
+    return false;
+}
+
+template <int W>
+__global__ void __launch_bounds__(SPLIT_THREADS) k_split(const Dev<W> a)
 {
     typedef typename Geo<W>::B B;
     constexpr int BITS = Geo<W>::BITS;
+    constexpr int SCAP = SplitShared<W>::CAP;
     __shared__ __align__(16) unsigned char lut[SharedLut<W>::BYTES];
+    __shared__ Rec<W> lvl[2][SCAP];
     __shared__ int warp_sums[32];
-    __shared__ int s_fmin, s_leaves_only;
+    __shared__ int s_fmin, s_last, s_carry;
     __shared__ unsigned long long s_internal;
 
-    const int k = blockIdx.x;
-    if (k >= a.ctrl->n_active)
-        return;
-    SharedLut<W>::load(lut, a.lut);
-    const unsigned inst = (a.ctrl->cur ? a.act1 : a.act0)[k];
-    const InstState<W> st = a.state[inst];
-    Rec<W> *A = a.scratch + (size_t)k * 2 * a.C;
-    Rec<W> *Bf = A + a.C;
-    const B GOAL = goal_board<W>();
-    if (threadIdx.x == 0) {
-        Rec<W> r;
-        r.b = st.root;
-        r.meta = st.root_meta & M_NODE_MASK;
-        if (r.b == GOAL)
-            r.meta |= M_LEAF;
-        r.inst = inst;
-        r.origin = 0;
-        r.pm = 0;
-        A[0] = r;
-        s_fmin = INT_MAX;
-        s_internal = 0;
-        a.cnt.search_nodes[inst] = 0;
-        a.cnt.goals[inst] = 0;
-        a.cnt.goal_origin[inst] = 0xffffffffu;
-    }
-    __syncthreads();
-
-    const int T = max(1, (int)st.target);
-    int cnt = 1, depth = 0;
-    Rec<W> *cur = A, *nxt = Bf;
-    for (;;) {
-        if (cnt >= T || depth >= 16 || 4 * cnt > a.C)
-            break;
-        // stop once every node of the level is a goal leaf
-        if (threadIdx.x == 0)
-            s_leaves_only = 1;
-        __syncthreads();
-        for (int j = threadIdx.x; j < cnt; j += blockDim.x)
-            if (!(cur[j].meta & M_LEAF))
-                s_leaves_only = 0;
-        __syncthreads();
-        if (s_leaves_only)
-            break;
-
-        int outbase = 0;
-        int fmin = INT_MAX;
-        unsigned long long internal = 0;
-        for (int base = 0; base < cnt; base += blockDim.x) {
-            const int j = base + threadIdx.x;
-            Rec<W> r;
-            r.meta = M_LEAF;
-            const bool v = j < cnt;
-            if (v)
-                r = cur[j];
-            const bool leaf = v && (r.meta & M_LEAF);
-            const bool exp = v && !leaf;
-            Rec<W> c[4];
-            int nc = 0;
-            if (leaf) {
-                c[0] = r;
-                nc = 1;
-            } else if (exp) {
-                internal += 1;
-                const int p = (int)m_blank(r.meta);
-                const int last = (int)m_last(r.meta);
-                const int s = m_slack(r.meta);
-                const uint32_t d = m_hi(r.meta);
-                const LutRow<W> e = SharedLut<W>::row(lut, p);
-#pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    if (!e.legal(m) || last == 3 - m)
-                        continue;
-                    const int np = p + move_off<W>(m);
-                    const unsigned t = tile_at<W>(r.b, np);
-                    const int s2 = e.away(m, t) ? s - 2 : s;
-                    if (s2 < 0) {
-                        fmin = min(fmin, -s2);
-                        continue;
-                    }
-                    const B x = (B)t;
-                    Rec<W> ch;
-                    ch.b = r.b + (x << (BITS * p)) - (x << (BITS * np));
-                    ch.meta = (uint32_t)np | ((uint32_t)m << 5) | ((uint32_t)s2 << 8) | ((d + 1u) << 16);
-                    if (ch.b == GOAL)
-                        ch.meta |= M_LEAF;
-                    ch.inst = inst;
-                    ch.origin = 0;
-                    ch.pm = r.pm | ((uint32_t)m << (2 * d));
-                    c[nc++] = ch;
-                }
-            }
-            int total;
-            const int pos = block_exclusive_scan(nc, warp_sums, &total);
-            for (int q = 0; q < nc; ++q)
-                nxt[outbase + pos + q] = c[q];
-            outbase += total;
-        }
-        fmin = warp_min_int(fmin);
-        if ((threadIdx.x & 31) == 0)
-            atomicMin(&s_fmin, fmin);
-        for (int d2 = 16; d2; d2 >>= 1)
-            internal += __shfl_xor_sync(FULL, internal, d2);
-        if ((threadIdx.x & 31) == 0)
-            atomicAdd(&s_internal, internal);
-        __syncthreads();
-        Rec<W> *t = cur;
-        cur = nxt;
-        nxt = t;
-        cnt = outbase;
-        ++depth;
-    }
-    if (cur != A) {
-        for (int j = threadIdx.x; j < cnt; j += blockDim.x)
-            A[j] = cur[j];
-    }
-    if (threadIdx.x == 0) {
-        a.count[k] = cnt;
-        a.cnt.split_nodes[inst] = s_internal;
-        a.cnt.fnext_off[inst] = s_fmin;
-    }
-}
-
-// Exclusive scan of the per-problem record counts (one block); opens the
-// step's first search pass.
-template <int W>
-__global__ void k_scan(const Dev<W> a)
-{
-    __shared__ int warp_sums[32];
-    __shared__ int carry;
     Ctrl *ctrl = a.ctrl;
-    const int n = ctrl->n_active;
+    const int k = blockIdx.x;
+    const int n_active = ctrl->n_active;
+    if (k < n_active) {
+        SharedLut<W>::load(lut, a.lut);
+        const unsigned inst = (ctrl->cur ? a.act1 : a.act0)[k];
+        const InstState<W> st = a.state[inst];
+        Rec<W> *A = a.scratch + (size_t)k * 2 * a.C;
+        Rec<W> *Bg = A + a.C;
+        const B GOAL = goal_board<W>();
+        if (threadIdx.x == 0) {
+            Rec<W> r;
+            r.b = st.root;
+            r.meta = st.root_meta & M_NODE_MASK;
+            if (r.b == GOAL)
+                r.meta |= M_LEAF;
+            r.inst = inst;
+            r.origin = 0;
+            r.pm = 0;
+            lvl[0][0] = r;
+            s_fmin = INT_MAX;
+            s_internal = 0;
+            a.cnt.search_nodes[inst] = 0;
+            a.cnt.goals[inst] = 0;
+            a.cnt.goal_origin[inst] = 0xffffffffu;
+        }
+        __syncthreads();
+
+        const int T = max(1, (int)st.target);
+        int cnt = 1, depth = 0;
+        int expandable = (st.root == GOAL) ? 0 : 1;
+        Rec<W> *cur = lvl[0];
+        for (;;) {
+            if (cnt >= T || depth >= 16 || 4 * cnt > a.C || expandable == 0)
+                break;
+            // the next level has at most 4*cnt records: shared memory if they fit
+            Rec<W> *nxt;
+            if (4 * cnt <= SCAP)
+                nxt = (cur == lvl[0]) ? lvl[1] : lvl[0];
+            else
+                nxt = (cur == A) ? Bg : A;
+            int outbase = 0, nonleaf = 0;
+            int fmin = INT_MAX;
+            unsigned long long internal = 0;
+            for (int base = 0; base < cnt; base += blockDim.x) {
+                const int j = base + threadIdx.x;
+                Rec<W> r;
+                r.meta = M_LEAF;
+                const bool v = j < cnt;
+                if (v)
+                    r = cur[j];
+                const bool leaf = v && (r.meta & M_LEAF);
+                const bool exp = v && !leaf;
+                Rec<W> c[4];
+                int nc = 0, nl = 0;
+                if (leaf) {
+                    c[0] = r;
+                    nc = 1;
+                } else if (exp) {
+                    internal += 1;
+                    const int p = (int)m_blank(r.meta);
+                    const int last = (int)m_last(r.meta);
+                    const int s = m_slack(r.meta);
+                    const uint32_t d = m_hi(r.meta);
+                    const LutRow<W> e = SharedLut<W>::row(lut, p);
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        if (!e.legal(m) || last == 3 - m)
+                            continue;
+                        const int np = p + move_off<W>(m);
+                        const unsigned t = tile_at<W>(r.b, np);
+                        const int s2 = e.away(m, t) ? s - 2 : s;
+                        if (s2 < 0) {
+                            fmin = min(fmin, -s2);
+                            continue;
+                        }
+                        const B x = (B)t;
+                        Rec<W> ch;
+                        ch.b = r.b + (x << (BITS * p)) - (x << (BITS * np));
+                        ch.meta = (uint32_t)np | ((uint32_t)m << 5) | ((uint32_t)s2 << 8) | ((d + 1u) << 16);
+                        if (ch.b == GOAL)
+                            ch.meta |= M_LEAF;
+                        else
+                            ++nl;
+                        ch.inst = inst;
+                        ch.origin = 0;
+                        ch.pm = r.pm | ((uint32_t)m << (2 * d));
+                        c[nc++] = ch;
+                    }
+                }
+                // one scan for both counts: records (low half), expandable records (high half)
+                int total;
+                const int pos = block_exclusive_scan(nc | (nl << 16), warp_sums, &total);
+                for (int q = 0; q < nc; ++q)
+                    nxt[outbase + (pos & 0xffff) + q] = c[q];
+                outbase += total & 0xffff;
+                nonleaf += total >> 16;
+            }
+            fmin = warp_min_int(fmin);
+            if ((threadIdx.x & 31) == 0)
+                atomicMin(&s_fmin, fmin);
+            for (int d2 = 16; d2; d2 >>= 1)
+                internal += __shfl_xor_sync(FULL, internal, d2);
+            if ((threadIdx.x & 31) == 0)
+                atomicAdd(&s_internal, internal);
+            __syncthreads();
+            cur = nxt;
+            cnt = outbase;
+            expandable = nonleaf;
+            ++depth;
+        }
+        if (cur != A) {
+            for (int j = threadIdx.x; j < cnt; j += blockDim.x)
+                A[j] = cur[j];
+        }
+        if (threadIdx.x == 0) {
+            a.count[k] = cnt;
+            a.cnt.split_nodes[inst] = s_internal;
+            a.cnt.fnext_off[inst] = s_fmin;
+        }
+    }
+    if (!last_block_done<W>((unsigned *)&ctrl->done_blocks, &s_last))
+        return;
+    // last block: frontier offsets, then open the first pass of the step
     if (threadIdx.x == 0)
-        carry = 0;
+        s_carry = 0;
     __syncthreads();
-    for (int base = 0; base < n; base += blockDim.x) {
+    for (int base = 0; base < n_active; base += blockDim.x) {
         const int j = base + threadIdx.x;
-        const int v = j < n ? a.count[j] : 0;
+        const int v = j < n_active ? __ldcg(&a.count[j]) : 0;
         int total;
         const int pos = block_exclusive_scan(v, warp_sums, &total);
-        if (j < n)
-            a.offset[j] = carry + pos;
+        if (j < n_active)
+            a.offset[j] = s_carry + pos;
         __syncthreads();
         if (threadIdx.x == 0)
-            carry += total;
+            s_carry += total;
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        ctrl->n_in = carry;
+        ctrl->done_blocks = 0;
+        ctrl->n_in = s_carry;
         ctrl->head = 0;
         ctrl->out_count = 0;
         ctrl->exited = 0;
         ctrl->qi = 0;
+        ctrl->first_pass = 1;
         ctrl->passes_step = 0;
         ctrl->t_start = ~0ull;
         ctrl->t_end = 0;
-        ctrl->records_total += (unsigned long long)carry;
+        ctrl->done_warps = 0;
+        ctrl->records_total += (unsigned long long)s_carry;
+        __threadfence();
         if (a.graph)
             cudaGraphSetConditional(a.h_pass, 1u);
     }
 }
 
-// Gather every problem's frontier into the first pass's queue; a record's
-// origin is its position in that queue.
+// End of a search pass (run by the search kernel's last warp): the records
+// handed back become the next pass's input; the pass loop ends when nothing
+// was handed back.
 template <int W>
-__global__ void k_compact(const Dev<W> a)
-{
-    const int k = blockIdx.x;
-    if (k >= a.ctrl->n_active)
-        return;
-    const Rec<W> *A = a.scratch + (size_t)k * 2 * a.C;
-    const int n = a.count[k], o = a.offset[k];
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        Rec<W> r = A[j];
-        r.origin = (uint32_t)(o + j);
-        a.q0[o + j] = r;
-    }
-}
-
-// After a search pass: the records handed back become the next pass's
-// input; the pass loop ends when nothing was handed back.
-template <int W>
-__global__ void k_pass_end(const Dev<W> a)
+__device__ void end_of_pass(const Dev<W> &a)
 {
     Ctrl *c = a.ctrl;
     c->passes_step += 1;
@@ -872,6 +923,8 @@ __global__ void k_pass_end(const Dev<W> a)
         c->search_ns += c->t_end - c->t_start;
     c->t_start = ~0ull;
     c->t_end = 0;
+    c->done_warps = 0;
+    c->first_pass = 0;
     c->max_out = max(c->max_out, c->out_count);
     if (c->passes_step >= MAX_PASSES_PER_STEP)
         c->err |= ERR_INTERNAL;
@@ -885,12 +938,14 @@ __global__ void k_pass_end(const Dev<W> a)
         c->exited = 0;
         c->qi ^= 1;
     }
+    __threadfence();
     if (a.graph)
         cudaGraphSetConditional(a.h_pass, again ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------
-// Advance: per problem, close the iteration (Algorithm 1's driver).
+// Advance: per problem, close the iteration (Algorithm 1's driver). The
+// last block closes the step: the problems still active form the next one.
 // ---------------------------------------------------------------------
 template <int W>
 __device__ bool take_goal_record(const Dev<W> &a, const CallDesc &dsc, int k, unsigned inst, InstState<W> &st)
@@ -926,118 +981,111 @@ __device__ bool take_goal_record(const Dev<W> &a, const CallDesc &dsc, int k, un
 template <int W>
 __global__ void k_advance(const Dev<W> a)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ int s_last;
     Ctrl *ctrl = a.ctrl;
-    if (k >= ctrl->n_active || ctrl->err)
-        return;
-    const CallDesc dsc = *a.desc;
-    const unsigned inst = (ctrl->cur ? a.act1 : a.act0)[k];
-    unsigned *next_active = ctrl->cur ? a.act0 : a.act1;
-    InstState<W> st = a.state[inst];
-    const unsigned long long total = a.cnt.split_nodes[inst] + a.cnt.search_nodes[inst];
-    const unsigned long long goals = a.cnt.goals[inst];
-    if (st.mode == MODE_COUNT) {
-        dsc.out_nodes[(size_t)inst * Geo<W>::MAXIT + st.it] = total;
-        st.rows = st.it + 1;
-        st.cum_nodes += total;
-        if (goals > 0) {
-            st.length = st.limit;
-            st.solutions = goals;
-            if (!take_goal_record<W>(a, dsc, k, inst, st)) {
-                st.mode = MODE_DONE;
-                st.status = 8;  // BPIDA_EINTERNAL
-                atomicOr(&ctrl->err, ERR_INTERNAL);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n_active = ctrl->n_active;
+    if (k < n_active && ctrl->err == 0) {
+        const CallDesc dsc = *a.desc;
+        const unsigned inst = (ctrl->cur ? a.act1 : a.act0)[k];
+        unsigned *next_active = ctrl->cur ? a.act0 : a.act1;
+        InstState<W> st = a.state[inst];
+        const unsigned long long total = a.cnt.split_nodes[inst] + a.cnt.search_nodes[inst];
+        const unsigned long long goals = a.cnt.goals[inst];
+        if (st.mode == MODE_COUNT) {
+            dsc.out_nodes[(size_t)inst * Geo<W>::MAXIT + st.it] = total;
+            st.rows = st.it + 1;
+            st.cum_nodes += total;
+            if (goals > 0) {
+                st.length = st.limit;
+                st.solutions = goals;
+                if (!take_goal_record<W>(a, dsc, k, inst, st)) {
+                    st.mode = MODE_DONE;
+                    st.status = 8;  // BPIDA_EINTERNAL
+                    atomicOr(&ctrl->err, ERR_INTERNAL);
+                }
+            } else {
+                const int off = a.cnt.fnext_off[inst];
+                if (off == INT_MAX || off <= 0) {
+                    st.mode = MODE_DONE;
+                    st.status = 8;
+                    atomicOr(&ctrl->err, ERR_INTERNAL);
+                } else if (dsc.node_budget && st.cum_nodes > dsc.node_budget) {
+                    st.mode = MODE_DONE;
+                    st.status = 4;  // BPIDA_EBUDGET
+                } else if (st.it + 1 >= Geo<W>::MAXIT || st.limit + off > Geo<W>::MAXLEN) {
+                    st.mode = MODE_DONE;
+                    st.status = 7;  // BPIDA_ELIMIT
+                } else {
+                    st.limit += off;
+                    st.it += 1;
+                    st.root = st.start;
+                    st.root_meta = m_make(m_blank(st.start_meta), LAST_NONE, (uint32_t)(st.limit - st.h0));
+                    unsigned long long want =
+                        (total * (unsigned long long)a.tune.growth) / (unsigned long long)a.tune.nodes_per_record;
+                    want = want < 1ull ? 1ull : want;
+                    want = want > (unsigned long long)a.tune.target_cap ? (unsigned long long)a.tune.target_cap : want;
+                    st.target = (uint32_t)want;
+                }
             }
-        } else {
-            const int off = a.cnt.fnext_off[inst];
-            if (off == INT_MAX || off <= 0) {
+        } else if (st.mode == MODE_PATH) {
+            if (goals == 0 || !take_goal_record<W>(a, dsc, k, inst, st)) {
                 st.mode = MODE_DONE;
                 st.status = 8;
                 atomicOr(&ctrl->err, ERR_INTERNAL);
-            } else if (dsc.node_budget && st.cum_nodes > dsc.node_budget) {
-                st.mode = MODE_DONE;
-                st.status = 4;  // BPIDA_EBUDGET
-            } else if (st.it + 1 >= Geo<W>::MAXIT || st.limit + off > Geo<W>::MAXLEN) {
-                st.mode = MODE_DONE;
-                st.status = 7;  // BPIDA_ELIMIT
-            } else {
-                st.limit += off;
-                st.it += 1;
-                st.root = st.start;
-                st.root_meta = m_make(m_blank(st.start_meta), LAST_NONE, (uint32_t)(st.limit - st.h0));
-                unsigned long long want =
-                    (total * (unsigned long long)a.tune.growth) / (unsigned long long)a.tune.nodes_per_record;
-                want = want < 1ull ? 1ull : want;
-                want = want > (unsigned long long)a.tune.target_cap ? (unsigned long long)a.tune.target_cap : want;
-                st.target = (uint32_t)want;
             }
         }
-    } else if (st.mode == MODE_PATH) {
-        if (goals == 0 || !take_goal_record<W>(a, dsc, k, inst, st)) {
-            st.mode = MODE_DONE;
-            st.status = 8;
-            atomicOr(&ctrl->err, ERR_INTERNAL);
+        a.state[inst] = st;
+        if (st.mode != MODE_DONE) {
+            const int j = atomicAdd(&ctrl->n_next, 1);
+            next_active[j] = inst;
+        } else if (a.done_list) {
+            a.done_list[atomicAdd(&ctrl->n_done, 1)] = inst;
         }
     }
-    a.state[inst] = st;
-    if (st.mode != MODE_DONE) {
-        const int j = atomicAdd(&ctrl->n_next, 1);
-        next_active[j] = inst;
-    }
-}
-
-// End of a threshold step: the problems still active form the next step.
-template <int W>
-__global__ void k_step_end(const Dev<W> a)
-{
-    Ctrl *c = a.ctrl;
-    c->n_active = c->n_next;
-    c->n_next = 0;
-    c->cur ^= 1;
-    c->steps += 1;
-    if (c->steps >= MAX_STEPS)
-        c->err |= ERR_INTERNAL;
-    c->step_again = (c->n_active > 0 && c->err == 0) ? 1 : 0;
-    if (a.graph)
-        cudaGraphSetConditional(a.h_step, (unsigned)c->step_again);
-}
-
-// ---------------------------------------------------------------------
-// Init / begin / finalize
-// ---------------------------------------------------------------------
-template <int W>
-__global__ void k_reset(const Dev<W> a)
-{
-    Ctrl *c = a.ctrl;
+    if (!last_block_done<W>((unsigned *)&ctrl->done_blocks, &s_last))
+        return;
     if (threadIdx.x == 0) {
-        Ctrl z;
-        memset(&z, 0, sizeof z);
-        z.t_start = ~0ull;
-        *c = z;
+        Ctrl *c = ctrl;
+        c->done_blocks = 0;
+        c->n_active = *(volatile int *)&c->n_next;
+        c->n_next = 0;
+        c->cur ^= 1;
+        c->steps += 1;
+        if (c->steps >= MAX_STEPS)
+            c->err |= ERR_INTERNAL;
+        c->step_again = (c->n_active > 0 && *(volatile int *)&c->err == 0) ? 1 : 0;
+        __threadfence();
+        if (a.graph)
+            cudaGraphSetConditional(a.h_step, (unsigned)c->step_again);
     }
 }
 
-static __global__ void k_set_desc(CallDesc d, CallDesc *dst) { *dst = d; }
+// ---------------------------------------------------------------------
+// Call set-up / init / finalize
+// ---------------------------------------------------------------------
+// Writes the call's arguments and clears the control block.
+static __global__ void k_set_desc(CallDesc d, CallDesc *dst, Ctrl *ctrl)
+{
+    *dst = d;
+    Ctrl z;
+    memset(&z, 0, sizeof z);
+    z.t_start = ~0ull;
+    *ctrl = z;
+}
 
+// Validates board b (permutation, parity class, h0 <= max length) and sets
+// up instance i: state, zeroed output rows. Returns true when the instance
+// is to be searched.
 template <int W>
-__global__ void k_init(const Dev<W> a)
+__device__ bool init_instance(const Dev<W> &a, const CallDesc &dsc, int i, typename Geo<W>::B b)
 {
     typedef typename Geo<W>::B B;
     constexpr int N = Geo<W>::N, BITS = Geo<W>::BITS;
-    const CallDesc dsc = *a.desc;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= dsc.n)
-        return;
     for (int j = 0; j < Geo<W>::MAXLEN; ++j)
         dsc.out_moves[(size_t)i * Geo<W>::MAXLEN + j] = 0;
     for (int j = 0; j < Geo<W>::MAXIT; ++j)
         dsc.out_nodes[(size_t)i * Geo<W>::MAXIT + j] = 0ull;
-    B b;
-    if constexpr (W <= 4) {
-        b = (B)dsc.boards[i];
-    } else {
-        b = (B)dsc.boards[2 * (size_t)i] | ((B)dsc.boards[2 * (size_t)i + 1] << 64);
-    }
     InstState<W> st;
     st.start = b;
     st.root = b;
@@ -1069,7 +1117,7 @@ __global__ void k_init(const Dev<W> a)
     }
     if constexpr (W != 4) {
         // bits above the last position must be clear
-        if ((b >> (BITS * N)) != 0)
+        if ((b >> (BITS * N)) != (B)0)
             ok = false;
     }
     if (ok) {
@@ -1096,17 +1144,58 @@ __global__ void k_init(const Dev<W> a)
         st.status = 0;
     }
     a.state[i] = st;
-    if (st.mode == MODE_COUNT) {
-        const int j = atomicAdd(&a.ctrl->n_active, 1);
-        a.act0[j] = (unsigned)i;
-    }
+    return st.mode == MODE_COUNT;
 }
 
 template <int W>
-__global__ void k_begin(const Dev<W> a)
+__device__ __forceinline__ typename Geo<W>::B load_board(const uint64_t *boards, size_t i)
 {
-    if (a.graph)
-        cudaGraphSetConditional(a.h_step, a.ctrl->n_active > 0 ? 1u : 0u);
+    typedef typename Geo<W>::B B;
+    if constexpr (W <= 4)
+        return (B)boards[i];
+    else
+        return (B)boards[2 * i] | ((B)boards[2 * i + 1] << 64);
+}
+
+template <int W>
+__global__ void k_init(const Dev<W> a)
+{
+    __shared__ int s_last;
+    const CallDesc dsc = *a.desc;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < dsc.n) {
+        if (init_instance<W>(a, dsc, i, load_board<W>(dsc.boards, i))) {
+            const int j = atomicAdd(&a.ctrl->n_active, 1);
+            a.act0[j] = (unsigned)i;
+        }
+    }
+    if (!last_block_done<W>((unsigned *)&a.ctrl->done_blocks, &s_last))
+        return;
+    if (threadIdx.x == 0) {
+        a.ctrl->done_blocks = 0;
+        __threadfence();
+        if (a.graph)
+            cudaGraphSetConditional(a.h_step, *(volatile int *)&a.ctrl->n_active > 0 ? 1u : 0u);
+    }
+}
+
+// Serving: admit new requests into free slots (slot[j] gets boards[j]) and
+// append the searchable ones to the current active list; the rest finish
+// at once (done list).
+template <int W>
+__global__ void k_admit(const Dev<W> a, const unsigned *slot, const uint64_t *boards, int count)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= count)
+        return;
+    const CallDesc dsc = *a.desc;
+    const unsigned i = slot[j];
+    if (init_instance<W>(a, dsc, (int)i, load_board<W>(boards, (size_t)j))) {
+        const int k = atomicAdd(&a.ctrl->n_active, 1);
+        (a.ctrl->cur ? a.act1 : a.act0)[k] = i;
+    } else {
+        a.done_list[atomicAdd(&a.ctrl->n_done, 1)] = i;
+    }
 }
 
 template <int W>

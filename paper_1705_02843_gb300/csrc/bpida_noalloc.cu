@@ -169,6 +169,7 @@ extern "C" bpida_status bpida_solve_noalloc(const uint64_t *boards, int n, int *
     d.tune.target_cap = NA_TCAP;
     d.tune.target_path = NA_TCAP;
     d.tune.growth = 8;
+    d.tune.min_pass_ns = 10000;
     d.lut = na_lut();
     d.graph = 0;
 
@@ -182,23 +183,19 @@ extern "C" bpida_status bpida_solve_noalloc(const uint64_t *boards, int n, int *
     desc.out_status = out_status;
     desc.n = n;
 
-    const dim3 b128(128), b256(256), b1024(1024), g_inst((n + 127) / 128);
+    const dim3 b128(128), bsplit(SPLIT_THREADS), g_inst((n + 127) / 128);
     Ctrl h;
-    k_set_desc<<<1, 1, 0, st>>>(desc, (CallDesc *)(base + OFF_DESC));
-    k_reset<4><<<1, 1, 0, st>>>(d);
+    k_set_desc<<<1, 1, 0, st>>>(desc, (CallDesc *)(base + OFF_DESC), d.ctrl);
     k_init<4><<<g_inst, b128, 0, st>>>(d);
     NA_CK(cudaGetLastError());
     NA_CK(cudaMemcpyAsync(&h, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     NA_CK(cudaStreamSynchronize(st));
     int n_active = h.n_active;
     while (n_active > 0) {
-        k_split<4><<<n_active, b256, 0, st>>>(d);
-        k_scan<4><<<1, b1024, 0, st>>>(d);
-        k_compact<4><<<n_active, b128, 0, st>>>(d);
+        k_split<4><<<n_active, bsplit, 0, st>>>(d);
         NA_CK(cudaGetLastError());
         for (;;) {
             k_search<4, NA_S><<<grid, threads, smem, st>>>(d);
-            k_pass_end<4><<<1, 1, 0, st>>>(d);
             NA_CK(cudaGetLastError());
             NA_CK(cudaMemcpyAsync(&h, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
             NA_CK(cudaStreamSynchronize(st));
@@ -206,7 +203,6 @@ extern "C" bpida_status bpida_solve_noalloc(const uint64_t *boards, int n, int *
                 break;
         }
         k_advance<4><<<(n_active + 127) / 128, b128, 0, st>>>(d);
-        k_step_end<4><<<1, 1, 0, st>>>(d);
         NA_CK(cudaGetLastError());
         NA_CK(cudaMemcpyAsync(&h, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
         NA_CK(cudaStreamSynchronize(st));

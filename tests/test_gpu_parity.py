@@ -112,6 +112,7 @@ def test_all_8puzzle_states():
     dict(split_target=1), dict(split_target=2, min_rounds=32, exit_fraction_pct=1),
     dict(split_target=64, exit_fraction_pct=90),
     dict(driver=1), dict(driver=1, split_target=1, stack_entries=1024),
+    dict(min_pass_us=-1, exit_fraction_pct=1, min_rounds=32), dict(min_pass_us=1000),
 ])
 def test_tuning_knobs_do_not_change_results(cfg):
     insts = I.walks15_16x40()[:8]
