@@ -61,7 +61,7 @@ struct Plan {
 };
 
 struct Workspace {
-    DevBuf state, act0, act1, ctr, scratch, count, offset, q0, q1, ctrl, desc;
+    DevBuf state, act0, act1, ctr, scratch, count, offset, q0, q1, ctrl, desc, ovf;
     Ctrl *h_ctrl = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     unsigned gen = 1;  // bumped whenever a buffer moves
@@ -87,7 +87,7 @@ struct Workspace {
         for (auto &kv : plans)
             kv.second.destroy();
         plans.clear();
-        DevBuf *all[] = {&state, &act0, &act1, &ctr, &scratch, &count, &offset, &q0, &q1, &ctrl, &desc};
+        DevBuf *all[] = {&state, &act0, &act1, &ctr, &scratch, &count, &offset, &q0, &q1, &ctrl, &desc, &ovf};
         for (DevBuf *b : all) {
             if (b->p)
                 cudaFree(b->p);
@@ -267,17 +267,18 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     g.total_warps = g.grid * cfg.wpb;
     g.tcap = cfg.split_target > 0 ? cfg.split_target : std::max(2, std::min(4096, (1 << 21) / std::max(n, 1)));
     g.C = 4 * g.tcap + 4;
-    // hand-back queue: every warp's stack plus its unfinished chunk, with
-    // room for overflow spills (each moves S/2 entries); overflowing it is
-    // detected and reported as BPIDA_ENOMEM
-    g.Q = std::max({(size_t)n * g.C, (size_t)g.total_warps * (S + 32) * 4, (size_t)1 << 24}) + 1024;
+    // per-warp overflow stacks, and the hand-back queue: every warp's shared
+    // and overflow stacks plus its unfinished chunk, twice over; overflowing
+    // it is detected and reported as BPIDA_ENOMEM
+    const int ovf_cap = (W == 5) ? 4 * S : 0;
+    g.Q = std::max({(size_t)n * g.C, (size_t)g.total_warps * (S + ovf_cap + 32) * 2, (size_t)1 << 24}) + 1024;
     if (g.Q > (size_t)INT_MAX / 2 || (size_t)n * 2 * g.C > (size_t)UINT32_MAX)
         return BPIDA_ENOMEM;
 
     CK(ws.ensure(ws.state, sizeof(InstState<W>) * n));
     CK(ws.ensure(ws.act0, sizeof(unsigned) * n));
     CK(ws.ensure(ws.act1, sizeof(unsigned) * n));
-    CK(ws.ensure(ws.ctr, (size_t)n * (3 * sizeof(unsigned long long) + sizeof(int) + sizeof(unsigned))));
+    CK(ws.ensure(ws.ctr, (size_t)n * (4 * sizeof(unsigned long long) + sizeof(int) + 2 * sizeof(unsigned))));
     CK(ws.ensure(ws.scratch, sizeof(Rec<W>) * (size_t)n * 2 * g.C));
     CK(ws.ensure(ws.count, sizeof(int) * n));
     CK(ws.ensure(ws.offset, sizeof(int) * n));
@@ -285,6 +286,7 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     CK(ws.ensure(ws.q1, sizeof(Rec<W>) * g.Q));
     CK(ws.ensure(ws.ctrl, sizeof(Ctrl)));
     CK(ws.ensure(ws.desc, sizeof(CallDesc)));
+    CK(ws.ensure(ws.ovf, (size_t)g.total_warps * ovf_cap * WarpStack<W>::ENTRY_BYTES));
     if (!ws.h_ctrl)
         CK(cudaMallocHost((void **)&ws.h_ctrl, sizeof(Ctrl)));
     if (!ws.ev0) {
@@ -306,6 +308,8 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     d.offset = (int *)ws.offset.p;
     d.C = g.C;
     d.Q = (int)g.Q;
+    d.ovf = (unsigned char *)ws.ovf.p;
+    d.ovf_cap = ovf_cap;
     {
         char *p = (char *)ws.ctr.p;
         d.cnt.search_nodes = (unsigned long long *)p;
@@ -314,9 +318,13 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
         p += sizeof(unsigned long long) * n;
         d.cnt.goals = (unsigned long long *)p;
         p += sizeof(unsigned long long) * n;
+        d.cnt.budget_left = (unsigned long long *)p;
+        p += sizeof(unsigned long long) * n;
         d.cnt.fnext_off = (int *)p;
         p += sizeof(int) * n;
         d.cnt.goal_origin = (unsigned *)p;
+        p += sizeof(unsigned) * n;
+        d.cnt.aborted = (unsigned *)p;
     }
     d.tune.min_rounds = cfg.min_rounds;
     d.tune.exit_threshold = std::max(1, (int)((long long)g.total_warps * cfg.exit_pct / 100));

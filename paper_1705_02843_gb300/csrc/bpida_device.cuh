@@ -222,6 +222,8 @@ struct Counters {
     int *fnext_off;                    // min over pruned children of f - limit
     unsigned long long *goals;         // goal nodes popped
     unsigned *goal_origin;             // smallest origin of a goal-bearing record
+    unsigned long long *budget_left;   // search nodes this iteration may pop (~0 = no budget)
+    unsigned *aborted;                 // the node budget ran out during this iteration
 };
 
 struct Tune {
@@ -306,6 +308,8 @@ template <int W> struct Dev {
     cudaGraphConditionalHandle h_step, h_pass;
     int graph;                  // 1 inside the CUDA graph (sets the loop conditions)
     unsigned *done_list;        // serving: instances that finished in this step (else null)
+    unsigned char *ovf;         // per-warp overflow stacks in global memory (may be null)
+    int ovf_cap;                // entries per warp overflow stack (0 = none)
 };
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -553,6 +557,14 @@ __global__ void k_search(const Dev<W> a)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpStack<W> stk;
     stk.init(smem + SharedLut<W>::BYTES + (size_t)warp * S * WarpStack<W>::ENTRY_BYTES, S);
+    // this warp's overflow stack in global memory: the oldest open nodes go
+    // there when the shared stack is full and come back when it drains
+    // (24-puzzle only: its deeper trees overflow the shared stack often)
+    constexpr bool OVF = (W == 5);
+    WarpStack<W> ovf;
+    const size_t gwarp = (size_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    ovf.init(a.ovf + gwarp * (size_t)a.ovf_cap * WarpStack<W>::ENTRY_BYTES, a.ovf_cap);
+    int ovf_n = 0;
     const unsigned lt = (1u << lane) - 1u;
     const B GOAL = goal_board<W>();
     const int n_in = a.ctrl->n_in;
@@ -581,24 +593,53 @@ __global__ void k_search(const Dev<W> a)
             const unsigned inst0 = __shfl_sync(FULL, inst, 0);
             const unsigned same = __ballot_sync(FULL, v && inst == inst0);
             const int cnt = (same == FULL) ? 32 : (__ffs(~same) - 1);
-            if (lane < cnt)
+            // an instance whose node budget ran out is dropped
+            const unsigned long long left = a.cnt.budget_left[inst0];
+            const bool budgeted = left != ~0ull;
+            const bool dropped = budgeted && *(volatile unsigned *)&a.cnt.aborted[inst0];
+            if (lane < cnt && !dropped)
                 stk.put(lane, r.b, sm_from_rec<W>(r.meta), r.origin);
-            int top = cnt;
+            int top = dropped ? 0 : cnt;
             __syncwarp();
-            unsigned long long nodes = 0;
+            unsigned long long nodes = 0, flushed = 0;
             int fmin = INT_MAX;
 
-            while (top > 0) {
+            while (top > 0 || (OVF && ovf_n > 0)) {
+                if (OVF && top == 0) {
+                    // refill from the overflow stack (its most recent spill)
+                    const int k = min(ovf_n, S / 2);
+                    for (int j = lane; j < k; j += 32) {
+                        B bb;
+                        uint32_t mm, oo;
+                        ovf.get(ovf_n - k + j, bb, mm, oo);
+                        stk.put(j, bb, mm, oo);
+                    }
+                    ovf_n -= k;
+                    top = k;
+                    __syncwarp();
+                }
                 const int n = min(32, top);
                 if (top + 3 * n > S) {
                     // keep room for up to 4n children (an instance root has
-                    // four): hand the oldest entries to the next pass and
-                    // move the rest down. Afterwards top <= max(n, S/2), so
+                    // four): move the oldest entries to the overflow stack,
+                    // or hand them to the next pass when it is full, and move
+                    // the rest down. Afterwards top <= max(n, S/2), so
                     // top + 3n <= S for S >= 256.
                     const int k = min(top - n, S / 2);
                     if (lane == 0)
                         atomicAdd(&a.ctrl->spills, 1ull);
-                    hand_back_stack<W, S>(a, out, stk, 0, k, inst0, lane);
+                    if (OVF && ovf_n + k <= a.ovf_cap) {
+                        for (int j = lane; j < k; j += 32) {
+                            B bb;
+                            uint32_t mm, oo;
+                            stk.get(j, bb, mm, oo);
+                            ovf.put(ovf_n + j, bb, mm, oo);
+                        }
+                        ovf_n += k;
+                    } else {
+                        hand_back_stack<W, S>(a, out, stk, 0, k, inst0, lane);
+                    }
+                    __syncwarp();
                     for (int j0 = 0; j0 < top - k; j0 += 32) {
                         const int j = j0 + lane;
                         const bool ok = j < top - k;
@@ -663,29 +704,51 @@ __global__ void k_search(const Dev<W> a)
                     fmin = min(fmin, 2 - s);
                 __syncwarp();
 
-                if (((++rounds) & 31) == 0 && rounds >= a.tune.min_rounds) {
-                    // hand back once enough warps have run dry and the pass
-                    // has run long enough to pay for another one
-                    int go = 0;
-                    if (lane == 0 && *(volatile int *)&a.ctrl->exited >= a.tune.exit_threshold)
-                        go = global_ns() - *(volatile unsigned long long *)&a.ctrl->t_start >=
-                             (unsigned long long)a.tune.min_pass_ns;
-                    if (__shfl_sync(FULL, go, 0)) {
-                        stop = true;
-                        break;
+                if (((++rounds) & 31) == 0) {
+                    if (budgeted) {
+                        // publish this run's count; past the budget the
+                        // instance's remaining work is dropped
+                        int over = 0;
+                        if (lane == 0) {
+                            const unsigned long long before = atomicAdd(&a.cnt.search_nodes[inst0], nodes - flushed);
+                            over = before + (nodes - flushed) > left;
+                            if (over)
+                                atomicExch(&a.cnt.aborted[inst0], 1u);
+                        }
+                        flushed = nodes;
+                        if (__shfl_sync(FULL, over, 0)) {
+                            top = 0;
+                            ovf_n = 0;
+                            break;
+                        }
+                    }
+                    if (rounds >= a.tune.min_rounds) {
+                        // hand back once enough warps have run dry and the
+                        // pass has run long enough to pay for another one
+                        int go = 0;
+                        if (lane == 0 && *(volatile int *)&a.ctrl->exited >= a.tune.exit_threshold)
+                            go = global_ns() - *(volatile unsigned long long *)&a.ctrl->t_start >=
+                                 (unsigned long long)a.tune.min_pass_ns;
+                        if (__shfl_sync(FULL, go, 0)) {
+                            stop = true;
+                            break;
+                        }
                     }
                 }
             }
             // flush this run's counters
             fmin = warp_min_int(fmin);
             if (lane == 0) {
-                atomicAdd(&a.cnt.search_nodes[inst0], nodes);
+                atomicAdd(&a.cnt.search_nodes[inst0], nodes - flushed);
                 atomicAdd(&a.ctrl->search_nodes_total, nodes);
                 if (fmin != INT_MAX)
                     atomicMin(&a.cnt.fnext_off[inst0], fmin);
             }
             if (stop) {
                 hand_back_stack<W, S>(a, out, stk, 0, top, inst0, lane);
+                if (OVF)
+                    hand_back_stack<W, S>(a, out, ovf, 0, ovf_n, inst0, lane);
+                ovf_n = 0;
                 hand_back_records<W>(a, frontier, n_act, in, out, i + cnt, end, lane);
                 break;
             }
@@ -777,6 +840,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split(const Dev<W> a)
             a.cnt.search_nodes[inst] = 0;
             a.cnt.goals[inst] = 0;
             a.cnt.goal_origin[inst] = 0xffffffffu;
+            a.cnt.aborted[inst] = 0;
         }
         __syncthreads();
 
@@ -871,6 +935,12 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split(const Dev<W> a)
             a.count[k] = cnt;
             a.cnt.split_nodes[inst] = s_internal;
             a.cnt.fnext_off[inst] = s_fmin;
+            // nodes the search may still pop in this iteration within the
+            // budget (counted iterations only; path recovery is not budgeted)
+            const unsigned long long budget = a.desc->node_budget;
+            const unsigned long long used = st.cum_nodes + s_internal;
+            a.cnt.budget_left[inst] = (budget == 0 || st.mode != MODE_COUNT) ? ~0ull
+                                                                             : (budget > used ? budget - used : 0ull);
         }
     }
     if (!last_block_done<W>((unsigned *)&ctrl->done_blocks, &s_last))
@@ -992,7 +1062,13 @@ __global__ void k_advance(const Dev<W> a)
         InstState<W> st = a.state[inst];
         const unsigned long long total = a.cnt.split_nodes[inst] + a.cnt.search_nodes[inst];
         const unsigned long long goals = a.cnt.goals[inst];
-        if (st.mode == MODE_COUNT) {
+        if (st.mode == MODE_COUNT && (a.cnt.aborted[inst] ||
+                                      (dsc.node_budget && st.cum_nodes + total > dsc.node_budget))) {
+            // the budget ran out inside this iteration: only the completed
+            // iterations are reported
+            st.mode = MODE_DONE;
+            st.status = 4;  // BPIDA_EBUDGET
+        } else if (st.mode == MODE_COUNT) {
             dsc.out_nodes[(size_t)inst * Geo<W>::MAXIT + st.it] = total;
             st.rows = st.it + 1;
             st.cum_nodes += total;
@@ -1010,9 +1086,6 @@ __global__ void k_advance(const Dev<W> a)
                     st.mode = MODE_DONE;
                     st.status = 8;
                     atomicOr(&ctrl->err, ERR_INTERNAL);
-                } else if (dsc.node_budget && st.cum_nodes > dsc.node_budget) {
-                    st.mode = MODE_DONE;
-                    st.status = 4;  // BPIDA_EBUDGET
                 } else if (st.it + 1 >= Geo<W>::MAXIT || st.limit + off > Geo<W>::MAXLEN) {
                     st.mode = MODE_DONE;
                     st.status = 7;  // BPIDA_ELIMIT

@@ -50,7 +50,7 @@ constexpr size_t OFF_DESC = OFF_CTRL + align256(sizeof(Ctrl));
 constexpr size_t OFF_STATE = OFF_DESC + align256(sizeof(CallDesc));
 constexpr size_t OFF_ACT0 = OFF_STATE + align256(sizeof(InstState<4>) * NA_N);
 constexpr size_t OFF_ACT1 = OFF_ACT0 + align256(sizeof(unsigned) * NA_N);
-constexpr size_t CTR_BYTES = (size_t)NA_N * (3 * sizeof(unsigned long long) + sizeof(int) + sizeof(unsigned));
+constexpr size_t CTR_BYTES = (size_t)NA_N * (4 * sizeof(unsigned long long) + sizeof(int) + 2 * sizeof(unsigned));
 constexpr size_t OFF_CTR = OFF_ACT1 + align256(sizeof(unsigned) * NA_N);
 constexpr size_t OFF_COUNT = OFF_CTR + align256(CTR_BYTES);
 constexpr size_t OFF_OFFSET = OFF_COUNT + align256(sizeof(int) * NA_N);
@@ -156,9 +156,13 @@ extern "C" bpida_status bpida_solve_noalloc(const uint64_t *boards, int n, int *
         p += sizeof(unsigned long long) * NA_N;
         d.cnt.goals = (unsigned long long *)p;
         p += sizeof(unsigned long long) * NA_N;
+        d.cnt.budget_left = (unsigned long long *)p;
+        p += sizeof(unsigned long long) * NA_N;
         d.cnt.fnext_off = (int *)p;
         p += sizeof(int) * NA_N;
         d.cnt.goal_origin = (unsigned *)p;
+        p += sizeof(unsigned) * NA_N;
+        d.cnt.aborted = (unsigned *)p;
     }
     const int grid = sms;
     const int threads = NA_WPB * 32;

@@ -309,7 +309,8 @@ bpida_server *bpida_server_create(const bpida_config *cfg, size_t frontier_bytes
     }
     sv->grid = sms * bpsm;
     const int total_warps = sv->grid * SV_WPB;
-    const size_t Q = std::max({(size_t)slots * C, (size_t)total_warps * (SV_S + 32) * 4, (size_t)1 << 24}) + 1024;
+    const int ovf_cap = 0;  // 15-puzzle: no overflow stacks
+    const size_t Q = std::max({(size_t)slots * C, (size_t)total_warps * (SV_S + ovf_cap + 32) * 2, (size_t)1 << 24}) + 1024;
 
     // one allocation carved into the workspace
     const size_t n = (size_t)slots;
@@ -321,12 +322,13 @@ bpida_server *bpida_server_create(const bpida_config *cfg, size_t frontier_bytes
     };
     const size_t o_ctrl = take(sizeof(Ctrl)), o_desc = take(sizeof(CallDesc));
     const size_t o_state = take(sizeof(InstState<SV_W>) * n), o_act0 = take(4 * n), o_act1 = take(4 * n);
-    const size_t o_ctr = take(n * (3 * 8 + 4 + 4)), o_count = take(4 * n), o_offset = take(4 * n);
+    const size_t o_ctr = take(n * (4 * 8 + 4 + 4 + 4)), o_count = take(4 * n), o_offset = take(4 * n);
     const size_t o_scr = take(sizeof(Rec<SV_W>) * n * 2 * C), o_q0 = take(sizeof(Rec<SV_W>) * Q),
                  o_q1 = take(sizeof(Rec<SV_W>) * Q);
     const size_t o_done = take(4 * n), o_aslot = take(4 * n), o_aboard = take(8 * n), o_packed = take(sizeof(Packed) * n);
     const size_t o_len = take(4 * n), o_moves = take(SV_MAXLEN * n), o_nodes = take(8 * SV_MAXIT * n),
                  o_iters = take(4 * n), o_status = take(4 * n);
+    const size_t o_ovf = take((size_t)total_warps * ovf_cap * WarpStack<SV_W>::ENTRY_BYTES);
     if (cudaMalloc(&sv->mem, off) != cudaSuccess) {
         delete sv;
         return nullptr;
@@ -346,6 +348,8 @@ bpida_server *bpida_server_create(const bpida_config *cfg, size_t frontier_bytes
     d.offset = (int *)(b + o_offset);
     d.C = C;
     d.Q = (int)Q;
+    d.ovf = (unsigned char *)(b + o_ovf);
+    d.ovf_cap = ovf_cap;
     {
         char *p = b + o_ctr;
         d.cnt.search_nodes = (unsigned long long *)p;
@@ -354,9 +358,13 @@ bpida_server *bpida_server_create(const bpida_config *cfg, size_t frontier_bytes
         p += 8 * n;
         d.cnt.goals = (unsigned long long *)p;
         p += 8 * n;
+        d.cnt.budget_left = (unsigned long long *)p;
+        p += 8 * n;
         d.cnt.fnext_off = (int *)p;
         p += 4 * n;
         d.cnt.goal_origin = (unsigned *)p;
+        p += 4 * n;
+        d.cnt.aborted = (unsigned *)p;
     }
     const int exit_pct = (cfg && cfg->exit_fraction_pct > 0) ? cfg->exit_fraction_pct : 10;
     d.tune.min_rounds = (cfg && cfg->min_rounds > 0) ? cfg->min_rounds : 64;

@@ -133,6 +133,38 @@ def test_node_budget():
         assert g["nodes"] == r.nodes[:len(g["nodes"])]
 
 
+@pytest.mark.parametrize("which", [0, 6, 14])
+def test_node_budget_boundary_matches_oracle(which):
+    """A budget equal to the oracle's total solves the board; one node less
+    must stop it, on the GPU as in the oracle, including when the budget runs
+    out in the middle of a large iteration."""
+    x = I.walks15_16x40()[which]
+    r = oracle.solve(4, x.tiles)
+    total = r.total_nodes
+    assert oracle.solve(4, x.tiles, node_budget=total).status == oracle.OK
+    assert oracle.solve(4, x.tiles, node_budget=total - 1).status == oracle.BUDGET
+    rc, got = gpu_solve(4, [x.tiles], node_budget=total)
+    assert got[0]["status"] == bpida.OK and got[0]["nodes"] == r.nodes
+    rc, got = gpu_solve(4, [x.tiles], node_budget=total - 1)
+    assert got[0]["status"] == bpida.EBUDGET and got[0]["nodes"] == r.nodes[:-1]
+    mid = sum(r.nodes[:-1]) + r.nodes[-1] // 3
+    rc, got = gpu_solve(4, [x.tiles], node_budget=mid)
+    assert got[0]["status"] == bpida.EBUDGET and got[0]["nodes"] == r.nodes[:-1]
+
+
+def test_budget_drops_only_the_instance_over_budget():
+    insts = I.walks15_16x40()[:6]
+    tiles = [x.tiles for x in insts]
+    ref = oracle.solve_batch(4, np.array(tiles, dtype=np.uint8))
+    budget = sorted(r.total_nodes for r in ref)[3]
+    rc, got = gpu_solve(4, tiles, node_budget=budget)
+    for g, r in zip(got, ref):
+        if r.total_nodes <= budget:
+            assert g["status"] == bpida.OK and g["nodes"] == r.nodes and g["moves"] == r.moves
+        else:
+            assert g["status"] == bpida.EBUDGET and g["nodes"] == r.nodes[:len(g["nodes"])]
+
+
 def test_24puzzle_walks():
     insts = [I.make_walk(5, 900 + s, 30 + 2 * s) for s in range(12)]
     tiles = [x.tiles for x in insts]
@@ -149,19 +181,63 @@ def _golden(name):
         return json.load(f)
 
 
-def test_perms15_100_sampled_cheap():
-    """Random permutations whose oracle results are stored, cheapest first."""
+def _check_golden(W, insts, got, recs):
+    """Compare with stored oracle results; boards the oracle stopped at its
+    node budget must stop on the GPU too, with the completed iterations
+    equal."""
+    checked = 0
+    for r in recs:
+        g = got[r["index"]]
+        assert g["status"] == r["status"], (r["index"], g["status"], r["status"])
+        if r["status"] == oracle.OK:
+            assert g["length"] == r["length"], r["index"]
+            assert g["nodes"] == r["nodes"], r["index"]
+            assert "".join(map(str, g["moves"])) == r["moves"], r["index"]
+            assert P.replay(W, insts[r["index"]].tiles, g["moves"]) == list(range(W * W))
+        else:
+            assert g["nodes"] == r["nodes"][:-1], r["index"]
+        checked += 1
+    return checked
+
+
+def test_perms15_100_full_plain_and_batched():
+    """All 100 random permutations, one solve call per board (the benchmark's
+    launch form) and all in one call."""
     doc = _golden("perms15_100")
     insts = I.perms15_100()
-    recs = sorted((r for r in doc["instances"] if r["status"] == 0), key=lambda r: sum(r["nodes"]))[:40]
-    tiles = [insts[r["index"]].tiles for r in recs]
-    rc, got = gpu_solve(4, tiles)
+    rc, batched = gpu_solve(4, [x.tiles for x in insts])
     assert rc == bpida.OK
-    for r, g, t in zip(recs, got, tiles):
-        assert g["length"] == r["length"]
-        assert g["nodes"] == r["nodes"]
-        assert "".join(map(str, g["moves"])) == r["moves"]
-        assert P.replay(4, t, g["moves"]) == list(range(16))
+    assert _check_golden(4, insts, batched, doc["instances"]) == 100
+    plain = []
+    for x in insts:
+        rc, g = gpu_solve(4, [x.tiles])
+        assert rc == bpida.OK
+        plain.extend(g)
+    assert plain == batched
+
+
+def test_mixed15_4096_full():
+    doc = _golden("mixed15_4096")
+    insts = I.mixed15_4096()
+    rc, got = gpu_solve(4, [x.tiles for x in insts])
+    assert rc == bpida.OK
+    assert _check_golden(4, insts, got, doc["instances"]) >= 4095
+    for i, (x, g) in enumerate(zip(insts, got)):
+        # properties that hold for every board, stored result or not
+        assert g["status"] == 0
+        assert P.replay(4, x.tiles, g["moves"]) == list(range(16))
+        if x.kind == "walk":
+            assert g["length"] <= x.walk_len and (x.walk_len - g["length"]) % 2 == 0
+
+
+def test_walks24_1024_with_node_budget():
+    doc = _golden("walks24_1024")
+    budget = doc["node_budget"]
+    insts = I.walks24_1024()
+    rc, got = gpu_solve(5, [x.tiles for x in insts], node_budget=budget)
+    assert rc == bpida.OK
+    assert _check_golden(5, insts, got, doc["instances"]) == 1024
+    assert sum(g["status"] == 0 for g in got) > 500
 
 
 def test_graph_and_host_drivers_agree_on_batch():
