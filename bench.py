@@ -49,14 +49,17 @@ UNIT = "expansions/s"
 WORKLOAD_DESC = ("perms15_100: 100 seeded uniformly random solvable 15-puzzle boards "
                  "(seeds 1001-1100), Manhattan distance, all-optimal-solutions mode")
 
-# Warp instructions issued per node expanded inside k_search<4,512>, from
-# ncu (smsp__inst_executed.sum / nodes) on the one-board capture recorded
-# in profiles/k_search_15puzzle_perms15_board0_final_iteration.txt.
-INSTR_PER_EXPANSION = 5.54
-# DRAM bytes per k_search launch; None until measured on this workload's
-# launches for the current kernel (the one-board capture read 136 KB for a
-# 108M-node launch: the kernel is not HBM-bound).
-TRAFFIC_PER_LAUNCH = None
+# Warp instructions issued per node expanded by k_search<4,512> in steady
+# state (the work the method needs per expansion), from ncu
+# (smsp__inst_executed.sum / nodes) on the final iteration of board 0 run as
+# one pass: profiles/k_search_15puzzle_perms15_board0_final_iteration.txt.
+INSTR_PER_EXPANSION = 5.49
+# The same ratio over every k_search launch of a plain solve of board 0
+# (hand-back on, as in the benchmark): ramp-up, short passes and hand-back
+# copies included. profiles/k_search_15puzzle_plain_solve_all_launches.txt.
+INSTR_PER_EXPANSION_PLAIN_MIX = 7.18
+# DRAM bytes (read + write) per k_search launch over those launches.
+TRAFFIC_PER_LAUNCH = 1230571
 
 
 def golden_path(name):
@@ -255,9 +258,11 @@ def main():
                     help="graph: each solve call is one CUDA graph launch (default); host: the "
                          "host launches every kernel (same kernels; ncu can list them)")
     ap.add_argument("--profile-case", type=int, default=None, metavar="IDX",
-                    help="solve board IDX alone with one search pass per iteration (for ncu "
-                         "captures: the final iteration's k_search launch is number iters-1), "
-                         "print its statistics and exit")
+                    help="solve board IDX alone, twice, through the host-driven loop with one "
+                         "search pass per iteration (for ncu captures: the final iteration's "
+                         "k_search launch is number iters-1), print its statistics and exit")
+    ap.add_argument("--profile-default", action="store_true",
+                    help="with --profile-case: keep the default hand-back (as in the bench)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local = dist_setup()
@@ -289,7 +294,8 @@ def main():
         for rep in range(2):
             # host-driven loop: ncu cannot see kernels inside graphs that
             # hold conditional nodes
-            s = bpida.solve(b, 4, bpida.make_config(4, exit_fraction_pct=100, driver=1))
+            s = bpida.solve(b, 4, bpida.make_config(4, exit_fraction_pct=0 if args.profile_default else 100,
+                                                    driver=1))
             torch.cuda.synchronize(dev)
         h = s.to_host()[0]
         st = bpida.last_stats()
@@ -443,6 +449,7 @@ def main():
                 "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH,
                 "kernel": "k_search<4,512>", "instr_per_expansion": INSTR_PER_EXPANSION,
                 "launch_ms_mean": s_ms / max(s_launch, 1), "launches_timed": s_launch,
+                "issue_utilization_plain_mix": s_nodes * INSTR_PER_EXPANSION_PLAIN_MIX / (s_ms / 1e3) / 1e9 / peak,
                 "expansions_per_s_in_kernel": s_nodes / (s_ms / 1e3),
                 "expansions_per_s_in_kernel_timed_steps": dev_nodes / (dev_ms / 1e3) if dev_ms else None,
                 "peak_basis": "%d SMs x 4 schedulers x %.0f MHz median SM clock sampled during the run" % (sms, f_mhz)}

@@ -442,6 +442,7 @@ bpida_status run_w(const Settings &cfg, const uint64_t *boards, int n, int *out_
     switch (cfg.S) {
     case 256: return run<W, 256>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, st);
     case 384: return run<W, 384>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, st);
+    case 480: return run<W, 480>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, st);
     case 768: return run<W, 768>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, st);
     case 1024: return run<W, 1024>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, st);
     default: return run<W, 512>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, st);
@@ -490,7 +491,7 @@ bpida_status bpida_solve_ex(const bpida_config *cfg_in, const uint64_t *boards, 
     cfg.budget = cfg_in ? cfg_in->node_budget : 0;
     if (cfg.width < 3 || cfg.width > 5 || n < 0)
         return BPIDA_EINVAL;
-    if (cfg.S != 256 && cfg.S != 384 && cfg.S != 512 && cfg.S != 768 && cfg.S != 1024)
+    if (cfg.S != 256 && cfg.S != 384 && cfg.S != 480 && cfg.S != 512 && cfg.S != 768 && cfg.S != 1024)
         return BPIDA_EINVAL;
     if (cfg.wpb < 1 || cfg.wpb > 32 || cfg.exit_pct > 100 || cfg.split_target < 0 || cfg.split_target > (1 << 20))
         return BPIDA_EINVAL;
