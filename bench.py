@@ -382,6 +382,29 @@ def main():
     if expansions(bsols) != exp_per_step:
         raise RuntimeError("batched and plain expansions differ")
 
+    # first-solution mode (Section 6's main timing experiment): each board
+    # stops at its first optimal solution
+    first_cfg = bpida.make_config(4, count_all=False, driver=1 if args.driver == "host" else 0)
+
+    def first_plain_step():
+        sols = []
+        for i in range(n):
+            s = bpida.solve(boards[i:i + 1], 4, first_cfg)
+            if s.status != bpida.OK:
+                raise RuntimeError("solve failed: " + bpida.status_str(s.status))
+            sols.append(s)
+        return sols, {}
+
+    def first_batched_step():
+        s = bpida.solve(boards, 4, first_cfg)
+        if s.status != bpida.OK:
+            raise RuntimeError("solve failed: " + bpida.status_str(s.status))
+        return [s], {}
+
+    ms_fp, _, fsols = timed(first_plain_step, max(1, args.steps // 2), 1)
+    ms_fb, _, _ = timed(first_batched_step, max(1, args.steps // 2), 1)
+    first_exp = expansions(fsols)
+
     # end to end through the host-buffer path (pinned boards, results back)
     host_boards = torch.from_numpy(packed.view(np.int64)).pin_memory()
     ml, mi = bpida.max_len(4), bpida.max_iters(4)
@@ -487,6 +510,10 @@ def main():
             "expansions_per_step": exp_per_step,
             "batched": {"value": b_value, "unit": UNIT, "instances_per_s": world * n * k / t_batch,
                         "ms_per_step": t_batch * 1e3 / k, "mode": "all 100 boards in one solve call"},
+            "first_solution": {"mode": "stop at the first optimal solution",
+                               "plain_instances_per_s": world * n * len(ms_fp) / (mx(sum(ms_fp)) / 1e3),
+                               "batched_instances_per_s": world * n * len(ms_fb) / (mx(sum(ms_fb)) / 1e3),
+                               "plain_expansions_per_step": first_exp},
             "parity": {"checked": checked, "mismatched": mismatched,
                        "against": "stored oracle results (length, per-iteration nodes, first solution)"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

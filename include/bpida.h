@@ -20,7 +20,13 @@
  *     the children pruned in the previous iteration (Algorithm 1);
  *   - with count_all = 1 the final iteration is searched to completion, as
  *     in the all-optimal-solutions experiment of Section 6, so its node
- *     count does not depend on the order in which nodes are expanded.
+ *     count does not depend on the order in which nodes are expanded, and
+ *     the solution returned is the lexicographically first optimal one;
+ *   - with count_all = 0 (first-solution mode, Section 6's main timing
+ *     experiment) an instance stops as soon as one of its warps pops a goal:
+ *     the non-final iterations' counts are unchanged, the final iteration's
+ *     count is what was expanded before the stop (it depends on timing), and
+ *     the solution returned is an optimal one, not necessarily the first.
  *
  * Board packing (device memory, read-only to the library):
  *   W = 3 or 4: one uint64_t per board, tile at position p in bits [4p, 4p+4).
@@ -64,7 +70,8 @@ typedef enum {
 
 typedef struct {
     int width;            /* 3, 4 or 5 (8-, 15-, 24-puzzle); 0 means 4 */
-    int count_all;        /* 1 = final iteration searched to completion */
+    int count_all;        /* 1 = final iteration searched to completion,
+                             0 = stop at the first solution found */
     int split_target;     /* max frontier records per instance; 0 = auto */
     int warps_per_block;  /* search kernel block size in warps; 0 = auto */
     int stack_entries;    /* per-warp shared-memory stack, 0 = auto

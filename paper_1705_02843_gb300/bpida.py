@@ -202,9 +202,10 @@ class Solution:
 
 def make_config(width: int = 4, split_target: int = 0, warps_per_block: int = 0,
                 stack_entries: int = 0, exit_fraction_pct: int = 0, min_rounds: int = 0,
-                node_budget: int = 0, driver: int = 0, min_pass_us: int = 0) -> Config:
-    return Config(width, 1, split_target, warps_per_block, stack_entries, exit_fraction_pct,
-                  min_rounds, node_budget, driver, min_pass_us)
+                node_budget: int = 0, driver: int = 0, min_pass_us: int = 0,
+                count_all: bool = True) -> Config:
+    return Config(width, 1 if count_all else 0, split_target, warps_per_block, stack_entries,
+                  exit_fraction_pct, min_rounds, node_budget, driver, min_pass_us)
 
 
 def solve(boards: torch.Tensor, width: int = 4, config: Optional[Config] = None,

@@ -345,6 +345,7 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     desc.out_status = out_status;
     desc.node_budget = cfg.budget;
     desc.n = n;
+    desc.first_only = cfg.count_all ? 0 : 1;
     k_set_desc<<<1, 1, 0, st>>>(desc, (CallDesc *)ws.desc.p, d.ctrl);
     CK(cudaGetLastError());
 
@@ -497,8 +498,8 @@ bpida_status bpida_solve_ex(const bpida_config *cfg_in, const uint64_t *boards, 
         return BPIDA_EINVAL;
     if (cfg.driver != 0 && cfg.driver != 1)
         return BPIDA_EINVAL;
-    if (cfg.count_all != 1)
-        return BPIDA_EINVAL;  // only the all-solutions mode is implemented
+    if (cfg.count_all != 0 && cfg.count_all != 1)
+        return BPIDA_EINVAL;
     if (n == 0)
         return BPIDA_OK;
     if (!boards || !out_len || !out_moves || !out_nodes_per_iter)

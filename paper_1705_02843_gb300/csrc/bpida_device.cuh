@@ -189,7 +189,7 @@ struct CallDesc {
     int *out_status;
     unsigned long long node_budget;
     int n;
-    int pad;
+    int first_only;  // 1: stop an instance's search at its first goal
 };
 
 static constexpr int ERR_QUEUE = 1;      // hand-back queue full
@@ -223,8 +223,10 @@ struct Counters {
     unsigned long long *goals;         // goal nodes popped
     unsigned *goal_origin;             // smallest origin of a goal-bearing record
     unsigned long long *budget_left;   // search nodes this iteration may pop (~0 = no budget)
-    unsigned *aborted;                 // the node budget ran out during this iteration
+    unsigned *aborted;                 // bit 0: the node budget ran out in this iteration;
+                                       // bit 1: first-solution mode found a goal
 };
+static constexpr unsigned ABORT_BUDGET = 1u, ABORT_FOUND = 2u;
 
 struct Tune {
     int min_rounds;      // rounds before a warp may hand its stack back
@@ -553,6 +555,7 @@ __global__ void k_search(const Dev<W> a)
     Rec<W> *out = a.ctrl->qi ? a.q0 : a.q1;
     const bool frontier = a.ctrl->first_pass != 0;
     const int n_act = a.ctrl->n_active;
+    const bool first_only = a.desc->first_only != 0;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpStack<W> stk;
@@ -593,10 +596,12 @@ __global__ void k_search(const Dev<W> a)
             const unsigned inst0 = __shfl_sync(FULL, inst, 0);
             const unsigned same = __ballot_sync(FULL, v && inst == inst0);
             const int cnt = (same == FULL) ? 32 : (__ffs(~same) - 1);
-            // an instance whose node budget ran out is dropped
+            // an instance whose node budget ran out, or that already found
+            // its goal in first-solution mode, is dropped
             const unsigned long long left = a.cnt.budget_left[inst0];
             const bool budgeted = left != ~0ull;
-            const bool dropped = budgeted && *(volatile unsigned *)&a.cnt.aborted[inst0];
+            const bool watch = budgeted || first_only;
+            const bool dropped = watch && *(volatile unsigned *)&a.cnt.aborted[inst0];
             if (lane < cnt && !dropped)
                 stk.put(lane, r.b, sm_from_rec<W>(r.meta), r.origin);
             int top = dropped ? 0 : cnt;
@@ -670,6 +675,8 @@ __global__ void k_search(const Dev<W> a)
                     if (lane == 0) {
                         atomicAdd(&a.cnt.goals[inst0], (unsigned long long)__popc(gmask));
                         atomicMin(&a.cnt.goal_origin[inst0], o);
+                        if (first_only)
+                            atomicOr(&a.cnt.aborted[inst0], ABORT_FOUND);
                     }
                 }
                 const uint32_t sh_p = mt & 127u;
@@ -705,6 +712,16 @@ __global__ void k_search(const Dev<W> a)
                 __syncwarp();
 
                 if (((++rounds) & 31) == 0) {
+                    if (first_only) {
+                        int found = 0;
+                        if (lane == 0)
+                            found = (*(volatile unsigned *)&a.cnt.aborted[inst0] & ABORT_FOUND) != 0;
+                        if (__shfl_sync(FULL, found, 0)) {
+                            top = 0;
+                            ovf_n = 0;
+                            break;
+                        }
+                    }
                     if (budgeted) {
                         // publish this run's count; past the budget the
                         // instance's remaining work is dropped
@@ -713,7 +730,7 @@ __global__ void k_search(const Dev<W> a)
                             const unsigned long long before = atomicAdd(&a.cnt.search_nodes[inst0], nodes - flushed);
                             over = before + (nodes - flushed) > left;
                             if (over)
-                                atomicExch(&a.cnt.aborted[inst0], 1u);
+                                atomicOr(&a.cnt.aborted[inst0], ABORT_BUDGET);
                         }
                         flushed = nodes;
                         if (__shfl_sync(FULL, over, 0)) {
@@ -1062,7 +1079,7 @@ __global__ void k_advance(const Dev<W> a)
         InstState<W> st = a.state[inst];
         const unsigned long long total = a.cnt.split_nodes[inst] + a.cnt.search_nodes[inst];
         const unsigned long long goals = a.cnt.goals[inst];
-        if (st.mode == MODE_COUNT && (a.cnt.aborted[inst] ||
+        if (st.mode == MODE_COUNT && ((a.cnt.aborted[inst] & ABORT_BUDGET) ||
                                       (dsc.node_budget && st.cum_nodes + total > dsc.node_budget))) {
             // the budget ran out inside this iteration: only the completed
             // iterations are reported

@@ -256,3 +256,24 @@ def test_repeated_plain_calls_reuse_the_graph():
         rc, got = gpu_solve(4, [x.tiles])
         assert rc == bpida.OK
         assert got[0]["nodes"] == r.nodes and got[0]["moves"] == r.moves
+
+
+def test_first_solution_mode():
+    """Stop at the first goal (Section 6's first-solution timing): optimal
+    length and every non-final iteration exact, the final iteration no larger
+    than in all-solutions mode, and the returned moves an optimal solution."""
+    doc = _golden("perms15_100")
+    cheap = sorted(doc["instances"], key=lambda r: sum(r["nodes"]))[:30]
+    perms = I.perms15_100()
+    insts = I.walks15_16x40() + [perms[r["index"]] for r in cheap]
+    tiles = [x.tiles for x in insts]
+    rc, got = gpu_solve(4, tiles, count_all=False)
+    assert rc == bpida.OK
+    ref = oracle.solve_batch(4, np.array(tiles, dtype=np.uint8), count_all=True)
+    first = oracle.solve_batch(4, np.array(tiles, dtype=np.uint8), count_all=False)
+    for t, g, r, f in zip(tiles, got, ref, first):
+        assert g["status"] == 0 and g["length"] == r.length == f.length
+        assert g["nodes"][:-1] == r.nodes[:-1] == f.nodes[:-1]
+        assert 1 <= g["nodes"][-1] <= r.nodes[-1]
+        assert len(g["moves"]) == g["length"]
+        assert P.replay(4, t, g["moves"]) == list(range(16))
