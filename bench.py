@@ -225,6 +225,56 @@ def run_serving(args):
                       "rates": out}), flush=True)
 
 
+def run_ablation(args):
+    """The paper's BPIDA* kernel (block = warp, 8 nodes x 4 actions per pop,
+    static root assignment, no dynamic load balancing) against this design,
+    on the same workloads and drivers; every result checked equal."""
+    import torch
+
+    from paper_1705_02843_gb300 import bpida
+
+    torch.cuda.set_device(0)
+    out = {}
+    for wl in ("perms15_100", "mixed15_4096"):
+        insts = I.WORKLOADS[wl]()
+        b = torch.from_numpy(I.packed_array(insts).view(np.int64)).cuda()
+        res = {}
+        wide = 65536 if wl == "perms15_100" else 512
+        for name, variant, split in (("this_design", 0, 0), ("paper_kernel", 1, 0),
+                                     ("paper_kernel_wide_roots", 1, wide)):
+            cfg = bpida.make_config(4, variant=variant, split_target=split)
+            forms = ("batched", "plain") if wl == "perms15_100" else ("batched",)
+            for form in forms:
+                for rep in range(2):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    if form == "batched":
+                        sols = [bpida.solve(b, 4, cfg)]
+                    else:
+                        sols = [bpida.solve(b[i:i + 1], 4, cfg) for i in range(len(insts))]
+                    torch.cuda.synchronize()
+                    dt = time.perf_counter() - t0
+                hosts = [h for s in sols for h in s.to_host()]
+                nodes = sum(sum(h["nodes"]) for h in hosts)
+                res[(name, form)] = (dt, nodes, [(h["length"], h["nodes"], h["moves"]) for h in hosts])
+        for form in ("batched", "plain"):
+            if ("this_design", form) not in res:
+                continue
+            a, p, q = res[("this_design", form)], res[("paper_kernel", form)], res[("paper_kernel_wide_roots", form)]
+            if a[2] != p[2] or a[2] != q[2]:
+                raise RuntimeError("kernels disagree on " + wl)
+            out["%s_%s" % (wl, form)] = {
+                "this_design_expansions_per_s": a[1] / a[0], "paper_kernel_expansions_per_s": p[1] / p[0],
+                "paper_kernel_wide_roots_expansions_per_s": q[1] / q[0],
+                "this_design_instances_per_s": len(insts) / a[0], "paper_kernel_instances_per_s": len(insts) / p[0],
+                "paper_kernel_wide_roots_instances_per_s": len(insts) / q[0],
+                "wide_roots_per_instance_cap": wide,
+                "speedup_vs_paper_kernel": p[0] / a[0], "speedup_vs_wide_roots": q[0] / a[0]}
+        print(json.dumps({wl: {k: v for k, v in out.items() if k.startswith(wl)}}), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "ablation: this design vs the paper's BPIDA* kernel (same driver, exact results)",
+                      "results": out}), flush=True)
+
+
 def pick_cpu_sample(insts, gold, budget_nodes):
     cores = os.cpu_count() or 1
     if gold:
@@ -249,6 +299,8 @@ def main():
     ap.add_argument("--workload", default="perms15_100", choices=["perms15_100"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-nodes", type=float, default=1.5e9)
+    ap.add_argument("--ablation", action="store_true",
+                    help="compare against the paper's BPIDA* kernel instead")
     ap.add_argument("--serving", action="store_true",
                     help="run the continuous-batching service under Poisson arrivals instead")
     ap.add_argument("--serving-rates", default="1000,2000,5000,10000,20000,50000")
@@ -272,6 +324,9 @@ def main():
         return
     if args.serving:
         run_serving(args)
+        return
+    if args.ablation:
+        run_ablation(args)
         return
 
     import torch

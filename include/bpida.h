@@ -89,6 +89,14 @@ typedef struct {
                              (needed for per-launch CUDA-event timing) */
     int min_pass_us;      /* a pass hands work back only after running this
                              long (microseconds); 0 = auto, -1 = no minimum */
+    int variant;          /* search kernel: 0 = warp per subtree group, one
+                             node per lane, work queue and hand-back
+                             (default); 1 = the paper's BPIDA* kernel
+                             (Algorithm 1: block = warp, 8 nodes per pop,
+                             lane i applies action i mod 4, roots assigned
+                             statically, no dynamic load balancing), kept as
+                             an ablation */
+    int reserved;
 } bpida_config;
 
 typedef struct {

@@ -39,6 +39,8 @@ class Config(ctypes.Structure):
         ("node_budget", ctypes.c_uint64),
         ("driver", ctypes.c_int),
         ("min_pass_us", ctypes.c_int),
+        ("variant", ctypes.c_int),
+        ("reserved", ctypes.c_int),
     ]
 
 
@@ -203,9 +205,9 @@ class Solution:
 def make_config(width: int = 4, split_target: int = 0, warps_per_block: int = 0,
                 stack_entries: int = 0, exit_fraction_pct: int = 0, min_rounds: int = 0,
                 node_budget: int = 0, driver: int = 0, min_pass_us: int = 0,
-                count_all: bool = True) -> Config:
+                count_all: bool = True, variant: int = 0) -> Config:
     return Config(width, 1 if count_all else 0, split_target, warps_per_block, stack_entries,
-                  exit_fraction_pct, min_rounds, node_budget, driver, min_pass_us)
+                  exit_fraction_pct, min_rounds, node_budget, driver, min_pass_us, variant, 0)
 
 
 def solve(boards: torch.Tensor, width: int = 4, config: Optional[Config] = None,

@@ -42,8 +42,8 @@ struct DevBuf {
     size_t n = 0;
 };
 
-// W, S, warps per block, n, frontier cap, hand-back percentage, min rounds, min pass time
-typedef std::tuple<int, int, int, int, int, int, int, int> PlanKey;
+// W, S, warps per block, n, frontier cap, hand-back percentage, min rounds, min pass time, variant
+typedef std::tuple<int, int, int, int, int, int, int, int, int> PlanKey;
 
 struct Plan {
     cudaGraph_t graph = nullptr;
@@ -146,7 +146,7 @@ template <int W> MoveLut<W> make_lut()
 }
 
 struct Settings {
-    int width, count_all, split_target, wpb, S, exit_pct, min_rounds, driver, min_pass_ns;
+    int width, count_all, split_target, wpb, S, exit_pct, min_rounds, driver, min_pass_ns, variant;
     uint64_t budget;
 };
 
@@ -192,7 +192,13 @@ struct Geometry {
     int grid, threads, total_warps, C, tcap;
     size_t smem, Q;
     int n_cap;
+    int variant;
 };
+
+template <int W, int S> void (*search_kernel(int variant))(const Dev<W>)
+{
+    return variant == 1 ? k_search_paper<W, S> : k_search<W, S>;
+}
 
 // The whole solve as one graph (k_set_desc is launched before it):
 //   init -> WHILE(step){ split -> WHILE(pass){ search } -> advance } -> finalize
@@ -234,8 +240,8 @@ cudaError_t build_graph(Plan &pl, Dev<W> d, const Geometry &g)
         return e;
 
     cudaGraphNode_t n_search;
-    if ((e = add_kernel(&n_search, P, nullptr, 0, k_search<W, S>, dim3(g.grid), dim3(g.threads), g.smem, d)) !=
-        cudaSuccess)
+    if ((e = add_kernel(&n_search, P, nullptr, 0, search_kernel<W, S>(g.variant), dim3(g.grid), dim3(g.threads),
+                        g.smem, d)) != cudaSuccess)
         return e;
     return cudaGraphInstantiate(&pl.exec, G, 0);
 }
@@ -252,19 +258,22 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
 
     Geometry g;
     g.n_cap = n;
-    g.threads = cfg.wpb * 32;
-    g.smem = SharedLut<W>::BYTES + (size_t)cfg.wpb * S * WarpStack<W>::ENTRY_BYTES;
-    // blocks of k_search per SM, looked up once per (device, W, S, block size)
-    static std::map<std::tuple<int, int>, int> occ;
-    int &bpsm = occ[std::make_tuple(dev, cfg.wpb)];
+    g.variant = cfg.variant;
+    const int wpb = cfg.variant == 1 ? 1 : cfg.wpb;  // the paper's kernel: block = warp
+    g.threads = wpb * 32;
+    g.smem = SharedLut<W>::BYTES + (size_t)wpb * S * WarpStack<W>::ENTRY_BYTES;
+    // blocks of the search kernel per SM, looked up once per (device, block size, variant)
+    static std::map<std::tuple<int, int, int>, int> occ;
+    int &bpsm = occ[std::make_tuple(dev, wpb, cfg.variant)];
     if (bpsm == 0) {
-        CK(cudaFuncSetAttribute(k_search<W, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem));
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_search<W, S>, g.threads, g.smem));
+        CK(cudaFuncSetAttribute(search_kernel<W, S>(cfg.variant), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)g.smem));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, search_kernel<W, S>(cfg.variant), g.threads, g.smem));
     }
     if (bpsm < 1)
         return BPIDA_EINVAL;
     g.grid = sms * bpsm;
-    g.total_warps = g.grid * cfg.wpb;
+    g.total_warps = g.grid * wpb;
     g.tcap = cfg.split_target > 0 ? cfg.split_target : std::max(2, std::min(4096, (1 << 21) / std::max(n, 1)));
     g.C = 4 * g.tcap + 4;
     // per-warp overflow stacks, and the hand-back queue: every warp's shared
@@ -358,7 +367,7 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     const dim3 b128(128), bsplit(SPLIT_THREADS);
     const dim3 g_inst((n + 127) / 128);
     if (cfg.driver == 0) {
-        const PlanKey key(W, S, cfg.wpb, n, g.tcap, cfg.exit_pct, cfg.min_rounds, cfg.min_pass_ns);
+        const PlanKey key(W, S, cfg.wpb, n, g.tcap, cfg.exit_pct, cfg.min_rounds, cfg.min_pass_ns, cfg.variant);
         Plan &pl = ws.plans[key];
         if (pl.exec && pl.gen != ws.gen)
             pl.destroy();
@@ -391,7 +400,7 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
             for (;;) {
                 if (g_timing)
                     CK(cudaEventRecord(ws.ev0, st));
-                k_search<W, S><<<g.grid, g.threads, g.smem, st>>>(d);
+                search_kernel<W, S>(cfg.variant)<<<g.grid, g.threads, g.smem, st>>>(d);
                 CK(cudaGetLastError());
                 if (g_timing)
                     CK(cudaEventRecord(ws.ev1, st));
@@ -487,6 +496,7 @@ bpida_status bpida_solve_ex(const bpida_config *cfg_in, const uint64_t *boards, 
     cfg.exit_pct = (cfg_in && cfg_in->exit_fraction_pct > 0) ? cfg_in->exit_fraction_pct : 10;
     cfg.min_rounds = (cfg_in && cfg_in->min_rounds > 0) ? cfg_in->min_rounds : 64;
     cfg.driver = cfg_in ? cfg_in->driver : 0;
+    cfg.variant = cfg_in ? cfg_in->variant : 0;
     cfg.min_pass_ns = (cfg_in && cfg_in->min_pass_us != 0) ? (cfg_in->min_pass_us < 0 ? 0 : cfg_in->min_pass_us * 1000)
                                                              : 10000;
     cfg.budget = cfg_in ? cfg_in->node_budget : 0;
@@ -497,6 +507,8 @@ bpida_status bpida_solve_ex(const bpida_config *cfg_in, const uint64_t *boards, 
     if (cfg.wpb < 1 || cfg.wpb > 32 || cfg.exit_pct > 100 || cfg.split_target < 0 || cfg.split_target > (1 << 20))
         return BPIDA_EINVAL;
     if (cfg.driver != 0 && cfg.driver != 1)
+        return BPIDA_EINVAL;
+    if (cfg.variant != 0 && cfg.variant != 1)
         return BPIDA_EINVAL;
     if (cfg.count_all != 0 && cfg.count_all != 1)
         return BPIDA_EINVAL;

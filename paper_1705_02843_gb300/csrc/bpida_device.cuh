@@ -790,6 +790,155 @@ __global__ void k_search(const Dev<W> a)
 }
 
 // ---------------------------------------------------------------------
+// The paper's BPIDA* kernel, kept as an ablation of the design above
+// (Algorithm 1 as printed): a block is one warp; each repetition pops
+// #threads / #actions = 8 nodes and lane i applies action (i mod 4) to node
+// i / 4; a child with f <= limit is pushed at a ballot-reserved slot
+// (atomicPut), the others only lower f_next. Roots are assigned to blocks
+// statically (block b takes an equal contiguous share of the root set) and
+// there is no dynamic load balancing; the root set is sized from the
+// previous iteration's work as for the main kernel. A full stack hands its
+// oldest entries to another pass (rare), which keeps the kernel exact.
+// ---------------------------------------------------------------------
+template <int W, int S>
+__global__ void __launch_bounds__(32) k_search_paper(const Dev<W> a)
+{
+    typedef typename Geo<W>::B B;
+    constexpr int BITS = Geo<W>::BITS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char *lut = smem;
+    if (threadIdx.x == 0)
+        atomicMin(&a.ctrl->t_start, global_ns());
+    SharedLut<W>::load(lut, a.lut);
+    __syncthreads();
+    const Rec<W> *in = a.ctrl->qi ? a.q1 : a.q0;
+    Rec<W> *out = a.ctrl->qi ? a.q0 : a.q1;
+    const bool frontier = a.ctrl->first_pass != 0;
+    const int n_act = a.ctrl->n_active;
+    const bool first_only = a.desc->first_only != 0;
+    const int lane = threadIdx.x & 31;
+    WarpStack<W> stk;
+    stk.init(smem + SharedLut<W>::BYTES, S);
+    const unsigned lt = (1u << lane) - 1u;
+    const int j = lane >> 2, m = lane & 3;  // node j of the pop, action m
+    const int n_in = a.ctrl->n_in;
+    // static share of the roots
+    const int share = (n_in + gridDim.x - 1) / gridDim.x;
+    const int r0 = min(n_in, blockIdx.x * share), r1 = min(n_in, r0 + share);
+    for (int i = r0; i < r1; ++i) {
+        const Rec<W> r = load_rec<W>(a, frontier, n_act, in, i);
+        const unsigned inst0 = r.inst;
+        const unsigned long long left = a.cnt.budget_left[inst0];
+        const bool budgeted = left != ~0ull;
+        if ((budgeted || first_only) && *(volatile unsigned *)&a.cnt.aborted[inst0])
+            continue;
+        if (lane == 0)
+            stk.put(0, r.b, sm_from_rec<W>(r.meta), r.origin);
+        int top = 1;
+        __syncwarp();
+        unsigned long long nodes = 0, flushed = 0;
+        int fmin = INT_MAX;
+        int rounds = 0;
+        while (top > 0) {
+            const int n = min(8, top);
+            if (top + 3 * n > S) {
+                const int k = min(top - n, S / 2);
+                if (lane == 0)
+                    atomicAdd(&a.ctrl->spills, 1ull);
+                hand_back_stack<W, S>(a, out, stk, 0, k, inst0, lane);
+                __syncwarp();
+                for (int j0 = 0; j0 < top - k; j0 += 32) {
+                    const int q = j0 + lane;
+                    const bool ok = q < top - k;
+                    B bb = 0;
+                    uint32_t mm = 0, oo = 0;
+                    if (ok)
+                        stk.get(k + q, bb, mm, oo);
+                    __syncwarp();
+                    if (ok)
+                        stk.put(q, bb, mm, oo);
+                    __syncwarp();
+                }
+                top -= k;
+            }
+            // parallelPop: the top n nodes, four lanes per node
+            const bool act = j < n;
+            B b = 0;
+            uint32_t mt = 0, org = 0;
+            if (act)
+                stk.get(top - n + j, b, mt, org);
+            top -= n;
+            nodes += (unsigned long long)n;
+            __syncwarp();
+            const bool goal = act && (b == goal_board<W>());
+            const unsigned gmask = __ballot_sync(FULL, goal && m == 0);
+            if (gmask) {
+                const unsigned o = warp_min_u32((goal && m == 0) ? org : 0xffffffffu);
+                if (lane == 0) {
+                    atomicAdd(&a.cnt.goals[inst0], (unsigned long long)__popc(gmask));
+                    atomicMin(&a.cnt.goal_origin[inst0], o);
+                    if (first_only)
+                        atomicOr(&a.cnt.aborted[inst0], ABORT_FOUND);
+                }
+            }
+            const uint32_t sh_p = mt & 127u;
+            const int s = (int)((mt >> 11) & 255u);
+            const bool legal = act && !goal && ((LegalMoves<W>::at_sh(sh_p) & ~((mt >> 7) & 15u)) >> m & 1u);
+            // the (threadID mod #actions)th action
+            const uint32_t sh_np = sh_p + (uint32_t)(BITS * move_off<W>(m));
+            const unsigned t = BoardOps<W>::tile(b, sh_np);
+            const LutRow<W> row = lut_row_sh<W>(lut, sh_p);
+            const bool away = away_bit<W>(row, m, t);
+            const bool push = legal && !(away && s < 2);
+            if (legal && away && s < 2)
+                fmin = min(fmin, 2 - s);
+            const B child = BoardOps<W>::flip(b, t * move_mul<W>(m), (m < 2) ? sh_np : sh_p);
+            const uint32_t cm = (sh_np + (mt & (255u << 11)) + ((1u << (3 - m)) << 7)) - (away ? (2u << 11) : 0u);
+            const unsigned pm = __ballot_sync(FULL, push);
+            if (push)
+                stk.put(top + __popc(pm & lt), child, cm, org);
+            top += __popc(pm);
+            __syncwarp();
+            if (((++rounds) & 31) == 0 && (budgeted || first_only)) {
+                int drop = 0;
+                if (lane == 0) {
+                    if (budgeted) {
+                        const unsigned long long before = atomicAdd(&a.cnt.search_nodes[inst0], nodes - flushed);
+                        if (before + (nodes - flushed) > left)
+                            atomicOr(&a.cnt.aborted[inst0], ABORT_BUDGET);
+                    }
+                    drop = *(volatile unsigned *)&a.cnt.aborted[inst0] != 0;
+                }
+                if (budgeted)
+                    flushed = nodes;
+                if (__shfl_sync(FULL, drop, 0)) {
+                    top = 0;
+                    break;
+                }
+            }
+        }
+        fmin = warp_min_int(fmin);
+        if (lane == 0) {
+            atomicAdd(&a.cnt.search_nodes[inst0], nodes - flushed);
+            atomicAdd(&a.ctrl->search_nodes_total, nodes);
+            if (fmin != INT_MAX)
+                atomicMin(&a.cnt.fnext_off[inst0], fmin);
+        }
+    }
+    // the last warp closes the pass (hand-back only from full stacks)
+    int last = 0;
+    if (lane == 0) {
+        atomicMax(&a.ctrl->t_end, global_ns());
+        __threadfence();
+        last = atomicAdd(&a.ctrl->done_warps, 1) == (int)gridDim.x - 1;
+    }
+    if (__shfl_sync(FULL, last, 0) && lane == 0) {
+        __threadfence();
+        end_of_pass<W>(a);
+    }
+}
+
+// ---------------------------------------------------------------------
 // Splitter: one block per problem; breadth-first, order-preserving
 // expansion of the problem's root until the level holds `target` records
 // (Algorithm 1's CreateRootSet, rebuilt every iteration). Nodes expanded

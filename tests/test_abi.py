@@ -44,4 +44,4 @@ def test_host_only_calls(lib):
 
 
 def test_config_struct_layout():
-    assert ctypes.sizeof(bpida.Config) == 7 * 4 + 4 + 8 + 8
+    assert ctypes.sizeof(bpida.Config) == 7 * 4 + 4 + 8 + 16

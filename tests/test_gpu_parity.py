@@ -113,6 +113,7 @@ def test_all_8puzzle_states():
     dict(split_target=64, exit_fraction_pct=90),
     dict(driver=1), dict(driver=1, split_target=1, stack_entries=1024),
     dict(min_pass_us=-1, exit_fraction_pct=1, min_rounds=32), dict(min_pass_us=1000),
+    dict(variant=1), dict(variant=1, driver=1), dict(variant=1, split_target=1),
 ])
 def test_tuning_knobs_do_not_change_results(cfg):
     insts = I.walks15_16x40()[:8]
@@ -277,3 +278,16 @@ def test_first_solution_mode():
         assert 1 <= g["nodes"][-1] <= r.nodes[-1]
         assert len(g["moves"]) == g["length"]
         assert P.replay(4, t, g["moves"]) == list(range(16))
+
+
+def test_paper_kernel_matches_on_permutations():
+    """The paper's BPIDA* kernel (ablation) gives the same exact results."""
+    doc = _golden("perms15_100")
+    cheap = sorted(doc["instances"], key=lambda r: sum(r["nodes"]))[:40]
+    perms = I.perms15_100()
+    insts = [perms[r["index"]] for r in cheap]
+    rc, got = gpu_solve(4, [x.tiles for x in insts], variant=1)
+    assert rc == bpida.OK
+    for r, g in zip(cheap, got):
+        assert g["length"] == r["length"] and g["nodes"] == r["nodes"]
+        assert "".join(map(str, g["moves"])) == r["moves"]
