@@ -142,11 +142,15 @@ bpida_status bpida_solve(const uint64_t *boards, int n, int *out_len, uint8_t *o
  * As bpida_solve, with a configuration and per-instance outputs:
  *   out_num_iters device, n ints: iterations run (may be NULL)
  *   out_status    device, n ints: bpida_status of each instance (may be NULL)
+ *   out_solutions device, n uint64: goals popped in the final iteration, i.e.
+ *                 with count_all = 1 the number of optimal solutions (move
+ *                 sequences of optimal length that never undo the previous
+ *                 move); with count_all = 0 at least 1 (may be NULL)
  * Row widths are bpida_max_len(cfg->width) and bpida_max_iters(cfg->width).
  */
 bpida_status bpida_solve_ex(const bpida_config *cfg, const uint64_t *boards, int n, int *out_len,
                             uint8_t *out_moves, uint64_t *out_nodes_per_iter, int *out_num_iters,
-                            int *out_status, void *stream);
+                            int *out_status, uint64_t *out_solutions, void *stream);
 
 /*
  * bpida_solve_noalloc — the 15-puzzle solve without any device allocation.
@@ -204,6 +208,7 @@ typedef struct {
     double done_time_s;         /* bpida_server_clock() when it became pollable */
     uint8_t moves[80];          /* first optimal solution, zero-filled */
     uint64_t nodes_per_iter[41];/* nodes expanded per iteration, zero-filled */
+    uint64_t solutions;         /* number of optimal solutions */
 } bpida_result;
 
 typedef struct {

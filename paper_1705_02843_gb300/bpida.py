@@ -76,6 +76,7 @@ class Result(ctypes.Structure):
         ("done_time_s", ctypes.c_double),
         ("moves", ctypes.c_uint8 * 80),
         ("nodes_per_iter", ctypes.c_uint64 * 41),
+        ("solutions", ctypes.c_uint64),
     ]
 
     def as_dict(self):
@@ -83,6 +84,7 @@ class Result(ctypes.Structure):
         return {"req_id": self.req_id, "status": self.status, "length": L,
                 "moves": list(self.moves[:max(L, 0)]), "iters": self.num_iters,
                 "nodes": list(self.nodes_per_iter[:self.num_iters]),
+                "solutions": self.solutions,
                 "latency_s": self.done_time_s - self.submit_time_s}
 
 
@@ -119,7 +121,7 @@ def load():
         lib.bpida_max_iters.restype = ctypes.c_int
         lib.bpida_solve.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp]
         lib.bpida_solve.restype = ctypes.c_int
-        lib.bpida_solve_ex.argtypes = [ctypes.POINTER(Config), vp, ctypes.c_int, vp, vp, vp, vp, vp, vp]
+        lib.bpida_solve_ex.argtypes = [ctypes.POINTER(Config), vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
         lib.bpida_solve_ex.restype = ctypes.c_int
         lib.bpida_set_timing.argtypes = [ctypes.c_int]
         lib.bpida_set_timing.restype = None
@@ -183,6 +185,7 @@ class Solution:
     nodes: torch.Tensor            # int64 (n, max_iters) (uint64 bit pattern)
     iters: torch.Tensor            # int32 (n,)
     inst_status: torch.Tensor      # int32 (n,)
+    solutions: Optional[torch.Tensor] = None  # int64 (n,): optimal solutions (count-all mode)
 
     def to_host(self):
         """Per-instance dicts with Python ints (moves trimmed to the length)."""
@@ -191,6 +194,7 @@ class Solution:
         nd = self.nodes.cpu().numpy().view("uint64")
         it = self.iters.cpu().tolist()
         stt = self.inst_status.cpu().tolist()
+        sol = self.solutions.cpu().tolist() if self.solutions is not None else [None] * len(L)
         out = []
         for i in range(len(L)):
             out.append({
@@ -198,6 +202,7 @@ class Solution:
                 "moves": [int(x) for x in mv[i, :max(L[i], 0)]],
                 "nodes": [int(x) for x in nd[i, :it[i]]],
                 "iters": it[i],
+                "solutions": sol[i],
             })
         return out
 
@@ -237,12 +242,13 @@ def solve(boards: torch.Tensor, width: int = 4, config: Optional[Config] = None,
     out_nodes = torch.empty((n, mi), dtype=torch.int64, device=dev)
     out_iters = torch.empty(n, dtype=torch.int32, device=dev)
     out_status = torch.empty(n, dtype=torch.int32, device=dev)
+    out_sol = torch.empty(n, dtype=torch.int64, device=dev)
     s = stream if stream is not None else torch.cuda.current_stream(dev)
     with torch.cuda.device(dev):
         rc = lib.bpida_solve_ex(ctypes.byref(cfg), boards.data_ptr(), n, out_len.data_ptr(),
                                 out_moves.data_ptr(), out_nodes.data_ptr(), out_iters.data_ptr(),
-                                out_status.data_ptr(), s.cuda_stream)
-    return Solution(rc, out_len, out_moves, out_nodes, out_iters, out_status)
+                                out_status.data_ptr(), out_sol.data_ptr(), s.cuda_stream)
+    return Solution(rc, out_len, out_moves, out_nodes, out_iters, out_status, out_sol)
 
 
 def solve_packed_host(packed, width: int = 4, config: Optional[Config] = None,

@@ -248,7 +248,7 @@ cudaError_t build_graph(Plan &pl, Dev<W> d, const Geometry &g)
 
 template <int W, int S>
 bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_len, uint8_t *out_moves,
-                 uint64_t *out_nodes, int *out_iters, int *out_status, cudaStream_t st)
+                 uint64_t *out_nodes, int *out_iters, int *out_status, uint64_t *out_solutions, cudaStream_t st)
 {
     int dev = 0;
     CK(cudaGetDevice(&dev));
@@ -352,6 +352,7 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     desc.out_nodes = (unsigned long long *)out_nodes;
     desc.out_iters = out_iters;
     desc.out_status = out_status;
+    desc.out_solutions = (unsigned long long *)out_solutions;
     desc.node_budget = cfg.budget;
     desc.n = n;
     desc.first_only = cfg.count_all ? 0 : 1;
@@ -447,15 +448,15 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
 
 template <int W>
 bpida_status run_w(const Settings &cfg, const uint64_t *boards, int n, int *out_len, uint8_t *out_moves,
-                   uint64_t *out_nodes, int *out_iters, int *out_status, cudaStream_t st)
+                   uint64_t *out_nodes, int *out_iters, int *out_status, uint64_t *out_sol, cudaStream_t st)
 {
     switch (cfg.S) {
-    case 256: return run<W, 256>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, st);
-    case 384: return run<W, 384>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, st);
-    case 480: return run<W, 480>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, st);
-    case 768: return run<W, 768>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, st);
-    case 1024: return run<W, 1024>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, st);
-    default: return run<W, 512>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, st);
+    case 256: return run<W, 256>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, out_sol, st);
+    case 384: return run<W, 384>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, out_sol, st);
+    case 480: return run<W, 480>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, out_sol, st);
+    case 768: return run<W, 768>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, out_sol, st);
+    case 1024: return run<W, 1024>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, out_sol, st);
+    default: return run<W, 512>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, out_sol, st);
     }
 }
 
@@ -485,7 +486,7 @@ int bpida_max_iters(int width)
 
 bpida_status bpida_solve_ex(const bpida_config *cfg_in, const uint64_t *boards, int n, int *out_len,
                             uint8_t *out_moves, uint64_t *out_nodes_per_iter, int *out_num_iters,
-                            int *out_status, void *stream)
+                            int *out_status, uint64_t *out_solutions, void *stream)
 {
     Settings cfg;
     cfg.width = (cfg_in && cfg_in->width) ? cfg_in->width : 4;
@@ -519,16 +520,22 @@ bpida_status bpida_solve_ex(const bpida_config *cfg_in, const uint64_t *boards, 
     std::lock_guard<std::mutex> lock(g_mu);
     cudaStream_t st = (cudaStream_t)stream;
     switch (cfg.width) {
-    case 3: return run_w<3>(cfg, boards, n, out_len, out_moves, out_nodes_per_iter, out_num_iters, out_status, st);
-    case 4: return run_w<4>(cfg, boards, n, out_len, out_moves, out_nodes_per_iter, out_num_iters, out_status, st);
-    default: return run_w<5>(cfg, boards, n, out_len, out_moves, out_nodes_per_iter, out_num_iters, out_status, st);
+    case 3:
+        return run_w<3>(cfg, boards, n, out_len, out_moves, out_nodes_per_iter, out_num_iters, out_status,
+                        out_solutions, st);
+    case 4:
+        return run_w<4>(cfg, boards, n, out_len, out_moves, out_nodes_per_iter, out_num_iters, out_status,
+                        out_solutions, st);
+    default:
+        return run_w<5>(cfg, boards, n, out_len, out_moves, out_nodes_per_iter, out_num_iters, out_status,
+                        out_solutions, st);
     }
 }
 
 bpida_status bpida_solve(const uint64_t *boards, int n, int *out_len, uint8_t *out_moves,
                          uint64_t *out_nodes_per_iter, void *stream)
 {
-    return bpida_solve_ex(nullptr, boards, n, out_len, out_moves, out_nodes_per_iter, nullptr, nullptr,
+    return bpida_solve_ex(nullptr, boards, n, out_len, out_moves, out_nodes_per_iter, nullptr, nullptr, nullptr,
                           stream);
 }
 

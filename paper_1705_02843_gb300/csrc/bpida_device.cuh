@@ -187,6 +187,7 @@ struct CallDesc {
     unsigned long long *out_nodes;
     int *out_iters;
     int *out_status;
+    unsigned long long *out_solutions;  // may be null
     unsigned long long node_budget;
     int n;
     int first_only;  // 1: stop an instance's search at its first goal
@@ -1453,6 +1454,8 @@ __global__ void k_finalize(const Dev<W> a)
         dsc.out_iters[i] = st.rows;
     if (dsc.out_status)
         dsc.out_status[i] = st.mode == MODE_DONE ? st.status : abort_status;
+    if (dsc.out_solutions)
+        dsc.out_solutions[i] = solved ? st.solutions : 0ull;
 }
 
 }  // namespace bp

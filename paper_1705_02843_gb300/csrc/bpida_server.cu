@@ -37,6 +37,7 @@ constexpr int SV_MAXIT = Geo<SV_W>::MAXIT;
 
 struct Packed {
     int len, iters, status, slot;
+    unsigned long long solutions;
     uint8_t moves[SV_MAXLEN];
     unsigned long long nodes[SV_MAXIT];
 };
@@ -61,6 +62,7 @@ __global__ void k_pack(const Dev<SV_W> a, Packed *out)
         o.iters = st.rows;
         o.status = st.mode == MODE_DONE ? st.status : 8;
         o.slot = (int)i;
+        o.solutions = solved ? st.solutions : 0ull;
     }
 }
 
@@ -218,6 +220,7 @@ bool bpida_server::device_step(int admitted)
             std::memcpy(r.moves, pk.moves, sizeof r.moves);
             for (int q = 0; q < SV_MAXIT; ++q)
                 r.nodes_per_iter[q] = pk.nodes[q];
+            r.solutions = pk.solutions;
             done.push_back(r);
             free_slots.push_back(pk.slot);
             --in_flight;

@@ -43,6 +43,7 @@ def check_against(W, tiles, got, ref):
         assert g["nodes"] == r.nodes, (i, g["nodes"], r.nodes)
         assert g["iters"] == r.iters
         assert g["moves"] == r.moves, (i, g["moves"], r.moves)
+        assert g["solutions"] == r.solutions, (i, g["solutions"], r.solutions)
         assert P.replay(W, tiles[i], g["moves"]) == list(range(W * W))
 
 
@@ -102,6 +103,8 @@ def test_all_8puzzle_states():
         assert g["length"] == dist[s]
         assert g["nodes"] == r.nodes, (i, g["nodes"], r.nodes)
         assert g["moves"] == r.moves
+        # all-solutions mode counts every shortest path (BFS path counting)
+        assert g["solutions"] == count[s], (i, g["solutions"], count[s])
     rs = random.Random(1)
     for i in rs.sample(range(len(order)), 2000):
         assert P.replay(3, tiles[i], got[i]["moves"]) == list(range(9))
@@ -194,6 +197,7 @@ def _check_golden(W, insts, got, recs):
             assert g["length"] == r["length"], r["index"]
             assert g["nodes"] == r["nodes"], r["index"]
             assert "".join(map(str, g["moves"])) == r["moves"], r["index"]
+            assert g["solutions"] == r["solutions"], r["index"]
             assert P.replay(W, insts[r["index"]].tiles, g["moves"]) == list(range(W * W))
         else:
             assert g["nodes"] == r["nodes"][:-1], r["index"]

@@ -64,6 +64,7 @@ def test_serving_matches_solo_results_in_the_mix():
         assert g["length"] == r["length"]
         assert g["nodes"] == r["nodes"]
         assert g["moves"] == r["moves"]
+        assert g["solutions"] == r["solutions"]
     ref = oracle.solve_batch(4, I.tiles_array(insts))
     for i, o in enumerate(ref):
         assert got[i]["length"] == o.length and got[i]["nodes"] == o.nodes and got[i]["moves"] == o.moves

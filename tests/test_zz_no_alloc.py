@@ -38,6 +38,8 @@ def test_noalloc_matches_solve_on_two_calls_in_a_row():
         assert ref.status == bpida.OK
         assert got.status == bpida.OK, bpida.status_str(got.status)
         r, g = ref.to_host(), got.to_host()
+        for x in r + g:
+            x.pop("solutions")  # only bpida_solve_ex reports solution counts
         assert g == r
         orc = oracle.solve_batch(4, I.tiles_array(insts), count_all=True)
         for gi, oi in zip(g, orc):
