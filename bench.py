@@ -134,6 +134,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value, pg=None, device=None):
+    """Largest value over the ranks of the process group (the job's time is
+    its slowest rank's); the identity without a process group."""
+    if pg is None:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, seconds_per_rank, world, pg=None, device=None):
+    """Whole-job throughput of N independent replicas: every rank processes
+    the same amount of work; the job takes as long as the slowest rank."""
+    t = max_over_ranks(seconds_per_rank, pg, device)
+    return world * units_per_rank / t
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -495,11 +514,7 @@ def main():
         raise RuntimeError("end-to-end expansions differ")
 
     def mx(v):
-        if pg is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(v, pg, dev)
 
     t_plain = mx(sum(ms_plain)) / 1e3
     t_batch = mx(sum(ms_batch)) / 1e3
