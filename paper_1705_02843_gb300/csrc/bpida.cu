@@ -49,6 +49,7 @@ struct Plan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     unsigned gen = 0;  // workspace generation the graph was built for
+    unsigned long long last_use = 0;
     void destroy()
     {
         if (exec)
@@ -66,6 +67,30 @@ struct Workspace {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     unsigned gen = 1;  // bumped whenever a buffer moves
     std::map<PlanKey, Plan> plans;
+    unsigned long long use_clock = 0;
+
+    // Keeps at most MAX_PLANS instantiated graphs (least recently used go
+    // first) and drops every graph built for buffers that have since moved.
+    static constexpr size_t MAX_PLANS = 8;
+    void trim_plans()
+    {
+        for (auto it = plans.begin(); it != plans.end();) {
+            if (!it->second.exec || it->second.gen != gen) {
+                it->second.destroy();
+                it = plans.erase(it);
+            } else {
+                ++it;
+            }
+        }
+        while (plans.size() >= MAX_PLANS) {
+            auto lru = plans.begin();
+            for (auto it = plans.begin(); it != plans.end(); ++it)
+                if (it->second.last_use < lru->second.last_use)
+                    lru = it;
+            lru->second.destroy();
+            plans.erase(lru);
+        }
+    }
 
     cudaError_t ensure(DevBuf &b, size_t bytes)
     {
@@ -203,14 +228,16 @@ template <int W, int S> void (*search_kernel(int variant))(const Dev<W>)
 // The whole solve as one graph (k_set_desc is launched before it):
 //   init -> WHILE(step){ split -> WHILE(pass){ search } -> advance } -> finalize
 template <int W, int S>
-cudaError_t build_graph(Plan &pl, Dev<W> d, const Geometry &g)
+cudaError_t build_graph(Plan &pl, Dev<W> d, const Geometry &g, const char **where)
 {
     cudaGraph_t G;
+    *where = "cudaGraphCreate";
     cudaError_t e = cudaGraphCreate(&G, 0);
     if (e != cudaSuccess)
         return e;
     pl.graph = G;
     cudaGraphConditionalHandle hs, hp;
+    *where = "step handle";
     if ((e = cudaGraphConditionalHandleCreate(&hs, G, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
         return e;
     d.graph = 1;
@@ -219,6 +246,7 @@ cudaError_t build_graph(Plan &pl, Dev<W> d, const Geometry &g)
     const dim3 b128(128), bsplit(SPLIT_THREADS);
     const dim3 g_inst((g.n_cap + 127) / 128), g_prob(g.n_cap);
     cudaGraphNode_t n_init, n_step, n_fin;
+    *where = "init/step/finalize nodes";
     if ((e = add_kernel(&n_init, G, nullptr, 0, k_init<W>, g_inst, b128, 0, d)) != cudaSuccess)
         return e;
     cudaGraph_t B;
@@ -227,10 +255,12 @@ cudaError_t build_graph(Plan &pl, Dev<W> d, const Geometry &g)
     if ((e = add_kernel(&n_fin, G, &n_step, 1, k_finalize<W>, g_inst, b128, 0, d)) != cudaSuccess)
         return e;
 
+    *where = "pass handle";
     if ((e = cudaGraphConditionalHandleCreate(&hp, B, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
         return e;
     d.h_pass = hp;
     cudaGraphNode_t n_split, n_pass, n_adv;
+    *where = "split/pass/advance nodes";
     if ((e = add_kernel(&n_split, B, nullptr, 0, k_split<W>, g_prob, bsplit, 0, d)) != cudaSuccess)
         return e;
     cudaGraph_t P;
@@ -240,9 +270,11 @@ cudaError_t build_graph(Plan &pl, Dev<W> d, const Geometry &g)
         return e;
 
     cudaGraphNode_t n_search;
+    *where = "search node";
     if ((e = add_kernel(&n_search, P, nullptr, 0, search_kernel<W, S>(g.variant), dim3(g.grid), dim3(g.threads),
                         g.smem, d)) != cudaSuccess)
         return e;
+    *where = "cudaGraphInstantiate";
     return cudaGraphInstantiate(&pl.exec, G, 0);
 }
 
@@ -262,14 +294,21 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     const int wpb = cfg.variant == 1 ? 1 : cfg.wpb;  // the paper's kernel: block = warp
     g.threads = wpb * 32;
     g.smem = SharedLut<W>::BYTES + (size_t)wpb * S * WarpStack<W>::ENTRY_BYTES;
-    // blocks of the search kernel per SM, looked up once per (device, block size, variant)
+    // one kernel serves every block size (and the serving path), so its
+    // dynamic shared memory limit is set once to the device's maximum; the
+    // blocks per SM are looked up once per (device, block size, variant)
+    static std::map<std::pair<int, int>, int> smem_limit;
+    int &lim = smem_limit[std::make_pair(dev, cfg.variant)];
+    if (lim == 0) {
+        CK(cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        CK(cudaFuncSetAttribute(search_kernel<W, S>(cfg.variant), cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    }
+    if (g.smem > (size_t)lim)
+        return BPIDA_EINVAL;
     static std::map<std::tuple<int, int, int>, int> occ;
     int &bpsm = occ[std::make_tuple(dev, wpb, cfg.variant)];
-    if (bpsm == 0) {
-        CK(cudaFuncSetAttribute(search_kernel<W, S>(cfg.variant), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)g.smem));
+    if (bpsm == 0)
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, search_kernel<W, S>(cfg.variant), g.threads, g.smem));
-    }
     if (bpsm < 1)
         return BPIDA_EINVAL;
     g.grid = sms * bpsm;
@@ -369,18 +408,23 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     const dim3 g_inst((n + 127) / 128);
     if (cfg.driver == 0) {
         const PlanKey key(W, S, cfg.wpb, n, g.tcap, cfg.exit_pct, cfg.min_rounds, cfg.min_pass_ns, cfg.variant);
-        Plan &pl = ws.plans[key];
-        if (pl.exec && pl.gen != ws.gen)
-            pl.destroy();
-        if (!pl.exec) {
-            cudaError_t e = build_graph<W, S>(pl, d, g);
+        auto found = ws.plans.find(key);
+        if (found == ws.plans.end() || !found->second.exec || found->second.gen != ws.gen) {
+            ws.trim_plans();
+            Plan &pl = ws.plans[key];
+            const char *where = "";
+            cudaError_t e = build_graph<W, S>(pl, d, g, &where);
             if (e != cudaSuccess) {
-                std::fprintf(stderr, "bpida: graph build failed: %s\n", cudaGetErrorString(e));
+                std::fprintf(stderr, "bpida: graph build failed at %s: %s\n", where, cudaGetErrorString(e));
                 pl.destroy();
+                ws.plans.erase(key);
                 return BPIDA_ECUDA;
             }
             pl.gen = ws.gen;
+            found = ws.plans.find(key);
         }
+        Plan &pl = found->second;
+        pl.last_use = ++ws.use_clock;
         CK(cudaGraphLaunch(pl.exec, st));
         CK(cudaMemcpyAsync(ws.h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));

@@ -301,8 +301,10 @@ bpida_server *bpida_server_create(const bpida_config *cfg, size_t frontier_bytes
     sv->max_slots = slots;
     sv->threads = SV_WPB * 32;
     sv->smem = SharedLut<SV_W>::BYTES + (size_t)SV_WPB * SV_S * WarpStack<SV_W>::ENTRY_BYTES;
-    int bpsm = 0;
-    if (cudaFuncSetAttribute(k_search<SV_W, SV_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv->smem) !=
+    int bpsm = 0, smem_max = 0;
+    // the device maximum, as the solve path sets it: the kernel is shared
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, sv->dev);
+    if (cudaFuncSetAttribute(k_search<SV_W, SV_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) !=
             cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_search<SV_W, SV_S>, sv->threads, sv->smem) !=
             cudaSuccess ||

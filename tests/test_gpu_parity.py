@@ -126,6 +126,32 @@ def test_tuning_knobs_do_not_change_results(cfg):
     check_against(4, tiles, got, oracle.solve_batch(4, np.array(tiles, dtype=np.uint8)))
 
 
+def test_block_size_changes_between_calls():
+    """The search kernel is shared by every block size: a call with small
+    blocks must not leave its shared-memory limit too low for the next call
+    with larger ones."""
+    insts = I.walks15_16x40()[:4]
+    tiles = [x.tiles for x in insts]
+    ref = oracle.solve_batch(4, np.array(tiles, dtype=np.uint8))
+    for wpb in (4, 1, 4, 8, 2, 8):
+        rc, got = gpu_solve(4, tiles, warps_per_block=wpb)
+        assert rc == bpida.OK, wpb
+        check_against(4, tiles, got, ref)
+
+
+def test_many_configurations_cycle_through_the_graph_cache():
+    """More distinct launch configurations than cached graphs: evicted
+    graphs are rebuilt on reuse and every call stays exact."""
+    insts = I.walks15_16x40()[:3]
+    tiles = [x.tiles for x in insts]
+    ref = oracle.solve_batch(4, np.array(tiles, dtype=np.uint8))
+    targets = [16, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768]
+    for st in targets + targets[:3]:
+        rc, got = gpu_solve(4, tiles, split_target=st)
+        assert rc == bpida.OK, st
+        check_against(4, tiles, got, ref)
+
+
 def test_node_budget():
     insts = I.walks15_16x40()[:2]
     tiles = [x.tiles for x in insts]
