@@ -300,7 +300,12 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     static std::map<std::pair<int, int>, int> smem_limit;
     int &lim = smem_limit[std::make_pair(dev, cfg.variant)];
     if (lim == 0) {
-        CK(cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        // the device maximum less the kernel's static shared memory
+        int optin = 0;
+        cudaFuncAttributes fa;
+        CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        CK(cudaFuncGetAttributes(&fa, search_kernel<W, S>(cfg.variant)));
+        lim = optin - (int)fa.sharedSizeBytes;
         CK(cudaFuncSetAttribute(search_kernel<W, S>(cfg.variant), cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     }
     if (g.smem > (size_t)lim)

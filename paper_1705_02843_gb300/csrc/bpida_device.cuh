@@ -165,7 +165,7 @@ struct Ctrl {
     int pass_again;   // set at the end of a pass: another pass follows
     int step_again;   // set at the end of a step: another step follows
     int first_pass;   // 1: this pass reads the splitter's frontiers in place
-    int done_warps;   // search warps finished in this pass
+    int done_warps;   // search blocks finished in this pass (one warp each in the paper kernel)
     int done_blocks;  // blocks finished in the current split / advance / init
     int n_done;       // serving: entries of the done list
     unsigned long long records_total;
@@ -547,9 +547,17 @@ __global__ void k_search(const Dev<W> a)
     typedef typename Geo<W>::B B;
     constexpr int BITS = Geo<W>::BITS;
     extern __shared__ __align__(16) unsigned char smem[];
+    // end-of-pass bookkeeping is combined per block, so that the grid-wide
+    // counters see one atomic per block instead of one per warp
+    __shared__ int s_warps_done;
+    __shared__ unsigned long long s_t_end, s_nodes;
     unsigned char *lut = smem;
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
         atomicMin(&a.ctrl->t_start, global_ns());
+        s_warps_done = 0;
+        s_t_end = 0;
+        s_nodes = 0;
+    }
     SharedLut<W>::load(lut, a.lut);
     __syncthreads();
     const Rec<W> *in = a.ctrl->qi ? a.q1 : a.q0;
@@ -576,6 +584,24 @@ __global__ void k_search(const Dev<W> a)
     const int chunk = max(1, min(32, n_in / (total_warps * 4)));
     int rounds = 0;
     bool stop = false;
+    // Node and pruned-f counters are accumulated per warp while its runs
+    // belong to one instance and published when the instance changes, when
+    // an instance has a node budget (its count gates the budget), and at the
+    // end: fmin is this lane's smallest pruned f - limit for acc_inst.
+    unsigned acc_inst = 0xffffffffu;
+    unsigned long long acc_nodes = 0, tot_nodes = 0;
+    int fmin = INT_MAX;
+    auto publish = [&]() {
+        const int fm = warp_min_int(fmin);
+        if (lane == 0 && acc_inst != 0xffffffffu) {
+            if (acc_nodes)
+                atomicAdd(&a.cnt.search_nodes[acc_inst], acc_nodes);
+            if (fm != INT_MAX)
+                atomicMin(&a.cnt.fnext_off[acc_inst], fm);
+        }
+        acc_nodes = 0;
+        fmin = INT_MAX;
+    };
 
     for (;;) {
         int h = 0;
@@ -606,9 +632,12 @@ __global__ void k_search(const Dev<W> a)
             if (lane < cnt && !dropped)
                 stk.put(lane, r.b, sm_from_rec<W>(r.meta), r.origin);
             int top = dropped ? 0 : cnt;
+            if (inst0 != acc_inst) {
+                publish();
+                acc_inst = inst0;
+            }
             __syncwarp();
             unsigned long long nodes = 0, flushed = 0;
-            int fmin = INT_MAX;
 
             while (top > 0 || (OVF && ovf_n > 0)) {
                 if (OVF && top == 0) {
@@ -754,14 +783,11 @@ __global__ void k_search(const Dev<W> a)
                     }
                 }
             }
-            // flush this run's counters
-            fmin = warp_min_int(fmin);
-            if (lane == 0) {
-                atomicAdd(&a.cnt.search_nodes[inst0], nodes - flushed);
-                atomicAdd(&a.ctrl->search_nodes_total, nodes);
-                if (fmin != INT_MAX)
-                    atomicMin(&a.cnt.fnext_off[inst0], fmin);
-            }
+            // this run's counts
+            acc_nodes += nodes - flushed;
+            tot_nodes += nodes;
+            if (budgeted)
+                publish();
             if (stop) {
                 hand_back_stack<W, S>(a, out, stk, 0, top, inst0, lane);
                 if (OVF)
@@ -775,18 +801,25 @@ __global__ void k_search(const Dev<W> a)
         if (stop)
             break;
     }
+    publish();
     if (!stop && lane == 0)
         atomicAdd(&a.ctrl->exited, 1);
-    // the last warp to finish closes the pass
-    int last = 0;
+    // the last warp of a block publishes the block's end time and node
+    // count; the last block to finish closes the pass
     if (lane == 0) {
-        atomicMax(&a.ctrl->t_end, global_ns());
+        atomicMax(&s_t_end, global_ns());
+        atomicAdd(&s_nodes, tot_nodes);
         __threadfence();
-        last = atomicAdd(&a.ctrl->done_warps, 1) == total_warps - 1;
-    }
-    if (__shfl_sync(FULL, last, 0) && lane == 0) {
-        __threadfence();
-        end_of_pass<W>(a);
+        if (atomicAdd(&s_warps_done, 1) == (int)(blockDim.x >> 5) - 1) {
+            __threadfence();
+            atomicMax(&a.ctrl->t_end, *(volatile unsigned long long *)&s_t_end);
+            atomicAdd(&a.ctrl->search_nodes_total, *(volatile unsigned long long *)&s_nodes);
+            __threadfence();
+            if (atomicAdd(&a.ctrl->done_warps, 1) == (int)gridDim.x - 1) {
+                __threadfence();
+                end_of_pass<W>(a);
+            }
+        }
     }
 }
 

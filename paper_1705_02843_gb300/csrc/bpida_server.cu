@@ -304,6 +304,9 @@ bpida_server *bpida_server_create(const bpida_config *cfg, size_t frontier_bytes
     int bpsm = 0, smem_max = 0;
     // the device maximum, as the solve path sets it: the kernel is shared
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, sv->dev);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_search<SV_W, SV_S>) == cudaSuccess)
+        smem_max -= (int)fa.sharedSizeBytes;  // less the kernel's static shared memory
     if (cudaFuncSetAttribute(k_search<SV_W, SV_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) !=
             cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_search<SV_W, SV_S>, sv->threads, sv->smem) !=
