@@ -95,7 +95,24 @@ typedef struct {
                              (Algorithm 1: block = warp, 8 nodes per pop,
                              lane i applies action i mod 4, roots assigned
                              statically, no dynamic load balancing), kept as
-                             an ablation */
+                             an ablation; 2, 3, 4 = the paper's thread-
+                             parallel configurations PSimple, PStaticLB and
+                             PFullLB (Section 4 and its appendix: one
+                             sequential depth-first search per thread over
+                             the roots assigned to it; no load balancing /
+                             static rebalancing of a persistent root set by
+                             the previous iteration's per-root loads / the
+                             same plus idle threads taking untried branches
+                             from busy threads of their block), kept as
+                             ablations. Variants 2-4 take width 3 or 4,
+                             count_all = 1 and no node budget (else
+                             BPIDA_EINVAL), solve the boards one at a time,
+                             use split_target as the number of search
+                             threads (0 = every resident thread) and report
+                             the load balance in bpida_stats; their
+                             solution is an optimal one (for 2 and 3 the
+                             lexicographically first), and every count
+                             equals variant 0's */
     int reserved;
 } bpida_config;
 
@@ -117,6 +134,17 @@ typedef struct {
     double search_ms_device;/* sum of search kernel durations measured on
                                the device (first block start to last block
                                end, %globaltimer), any driver */
+    /* thread-parallel variants (2-4) only, zero otherwise: */
+    int tp_threads;         /* search threads */
+    int tp_pad;
+    double lb_ratio;        /* load balance of the last board's next-to-last
+                               iteration (its only one if it had one): the
+                               largest per-thread node count over the mean
+                               over all search threads */
+    double lb_ratio_last;   /* the same for its final iteration */
+    uint64_t tp_roots;      /* roots in the last board's final root set */
+    uint64_t tp_balances;   /* variant 4: in-block balancing operations */
+    uint64_t tp_steals;     /* variant 4: branches moved to idle threads */
 } bpida_stats;
 
 /* Upper bounds used to size the per-instance output rows. */
@@ -132,8 +160,10 @@ int bpida_max_iters(int width);  /* iterations per node-count row */
  *                      the order up < left < right < down), zero-filled
  *   out_nodes_per_iter device, n * bpida_max_iters(4) uint64: nodes
  *                      expanded in each iteration, zero-filled
- * Returns BPIDA_OK if every instance was solved, otherwise the first error
- * code met (per-instance codes are available through bpida_solve_ex).
+ * Returns BPIDA_OK unless the call itself failed (a bad argument, a CUDA
+ * error, workspace or queue capacity, an internal check); what happened to
+ * each instance (solved, unsolvable board, length cap, node budget) is its
+ * out_len / out_status entry (bpida_solve_ex).
  */
 bpida_status bpida_solve(const uint64_t *boards, int n, int *out_len, uint8_t *out_moves,
                          uint64_t *out_nodes_per_iter, void *stream);

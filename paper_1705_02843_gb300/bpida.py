@@ -17,6 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbpida.so")
 
 OK, EINVAL, ENOMEM, ESTACK, EBUDGET, ETIMEOUT, ECUDA, ELIMIT, EINTERNAL = range(9)
+# bpida_config.variant values
+BLOCK_PARALLEL, PAPER_KERNEL, PSIMPLE, PSTATICLB, PFULLLB = range(5)
 
 EXPORTS = (
     "bpida_max_len", "bpida_max_iters", "bpida_solve", "bpida_solve_ex", "bpida_set_timing",
@@ -59,6 +61,13 @@ class Stats(ctypes.Structure):
         ("spills", ctypes.c_uint64),
         ("max_handed_back", ctypes.c_int),
         ("search_ms_device", ctypes.c_double),
+        ("tp_threads", ctypes.c_int),
+        ("tp_pad", ctypes.c_int),
+        ("lb_ratio", ctypes.c_double),
+        ("lb_ratio_last", ctypes.c_double),
+        ("tp_roots", ctypes.c_uint64),
+        ("tp_balances", ctypes.c_uint64),
+        ("tp_steals", ctypes.c_uint64),
     ]
 
     def as_dict(self):

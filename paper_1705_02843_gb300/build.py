@@ -7,8 +7,10 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libbpida.so")
-SOURCES = [os.path.join(HERE, "csrc", n) for n in ("bpida.cu", "bpida_noalloc.cu", "bpida_server.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", "bpida_device.cuh"), os.path.join(ROOT, "include", "bpida.h")]
+SOURCES = [os.path.join(HERE, "csrc", n) for n in ("bpida.cu", "bpida_noalloc.cu", "bpida_server.cu",
+                                                   "bpida_thread.cu")]
+DEPS = SOURCES + [os.path.join(HERE, "csrc", n) for n in ("bpida_device.cuh", "bpida_thread.h")] + [
+    os.path.join(ROOT, "include", "bpida.h")]
 
 NVCC_FLAGS = [
     "-O3", "-std=c++17",

@@ -19,6 +19,7 @@
 // search launch with CUDA events.
 #include "bpida.h"
 #include "bpida_device.cuh"
+#include "bpida_thread.h"
 
 #include <algorithm>
 #include <cstdio>
@@ -140,34 +141,6 @@ Workspace *workspace_for(int dev)
     if (!g_ws[dev])
         g_ws[dev] = new Workspace();
     return g_ws[dev];
-}
-
-// Manhattan move table (see MoveLut): for blank position p and move m,
-// bit 0 = legal, bit t = tile t moves away from its goal cell.
-template <int W> MoveLut<W> make_lut()
-{
-    MoveLut<W> L;
-    std::memset(&L, 0, sizeof L);
-    const int N = W * W;
-    const int dr[4] = {-1, 0, 0, 1}, dc[4] = {0, -1, 1, 0};
-    for (int p = 0; p < N; ++p) {
-        const int r = p / W, c = p % W;
-        for (int m = 0; m < 4; ++m) {
-            const int rr = r + dr[m], cc = c + dc[m];
-            if (rr < 0 || rr >= W || cc < 0 || cc >= W)
-                continue;
-            uint32_t e = 1u;
-            for (int t = 1; t < N; ++t) {
-                const int gr = t / W, gc = t % W;
-                const int before = std::abs(rr - gr) + std::abs(cc - gc);
-                const int after = std::abs(r - gr) + std::abs(c - gc);
-                if (after > before)
-                    e |= 1u << t;
-            }
-            L.e[p][m] = e;
-        }
-    }
-    return L;
 }
 
 struct Settings {
@@ -386,7 +359,7 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     d.tune.target_path = std::min(g.tcap, 4096);
     d.tune.growth = 8;
     d.tune.min_pass_ns = cfg.min_pass_ns;
-    d.lut = make_lut<W>();
+    d.lut = make_move_lut<W>();
 
     CallDesc desc;
     std::memset(&desc, 0, sizeof desc);
@@ -558,7 +531,9 @@ bpida_status bpida_solve_ex(const bpida_config *cfg_in, const uint64_t *boards, 
         return BPIDA_EINVAL;
     if (cfg.driver != 0 && cfg.driver != 1)
         return BPIDA_EINVAL;
-    if (cfg.variant != 0 && cfg.variant != 1)
+    if (cfg.variant < 0 || cfg.variant > tp::PFULLLB)
+        return BPIDA_EINVAL;
+    if (cfg.variant >= tp::PSIMPLE && (cfg.width == 5 || cfg.count_all != 1 || cfg.budget != 0))
         return BPIDA_EINVAL;
     if (cfg.count_all != 0 && cfg.count_all != 1)
         return BPIDA_EINVAL;
@@ -568,6 +543,18 @@ bpida_status bpida_solve_ex(const bpida_config *cfg_in, const uint64_t *boards, 
         return BPIDA_EINVAL;
     std::lock_guard<std::mutex> lock(g_mu);
     cudaStream_t st = (cudaStream_t)stream;
+    if (cfg.variant >= tp::PSIMPLE) {
+        tp::Settings ts;
+        ts.width = cfg.width;
+        ts.variant = cfg.variant;
+        ts.threads = cfg.split_target;
+        bpida_stats stats;
+        std::memset(&stats, 0, sizeof stats);
+        const bpida_status r = tp::solve(ts, boards, n, out_len, out_moves, out_nodes_per_iter, out_num_iters,
+                                         out_status, out_solutions, st, &stats);
+        g_stats = stats;
+        return r;
+    }
     switch (cfg.width) {
     case 3:
         return run_w<3>(cfg, boards, n, out_len, out_moves, out_nodes_per_iter, out_num_iters, out_status,
@@ -604,6 +591,7 @@ void bpida_release_workspace(void)
         return;
     if (dev < (int)g_ws.size() && g_ws[dev])
         g_ws[dev]->release();
+    tp::release(dev);
 }
 
 const char *bpida_status_str(int s)

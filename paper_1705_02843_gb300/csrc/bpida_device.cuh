@@ -96,6 +96,35 @@ template <int W> struct Rec {
 //                it away from its goal cell (h rises by 1; else h falls by 1)
 template <int W> struct MoveLut { uint32_t e[Geo<W>::N][4]; };
 
+// Builds the table on the host (Manhattan distance of tile t from its goal
+// cell before and after it slides into the blank).
+template <int W> inline MoveLut<W> make_move_lut()
+{
+    MoveLut<W> L;
+    for (int p = 0; p < Geo<W>::N; ++p)
+        for (int m = 0; m < 4; ++m)
+            L.e[p][m] = 0u;
+    const int dr[4] = {-1, 0, 0, 1}, dc[4] = {0, -1, 1, 0};
+    for (int p = 0; p < W * W; ++p) {
+        const int r = p / W, c = p % W;
+        for (int m = 0; m < 4; ++m) {
+            const int rr = r + dr[m], cc = c + dc[m];
+            if (rr < 0 || rr >= W || cc < 0 || cc >= W)
+                continue;
+            uint32_t e = 1u;
+            for (int t = 1; t < W * W; ++t) {
+                const int gr = t / W, gc = t % W;
+                const int before = (rr > gr ? rr - gr : gr - rr) + (cc > gc ? cc - gc : gc - cc);
+                const int after = (r > gr ? r - gr : gr - r) + (c > gc ? c - gc : gc - c);
+                if (after > before)
+                    e |= 1u << t;
+            }
+            L.e[p][m] = e;
+        }
+    }
+    return L;
+}
+
 // Per-lane view of one table row. W <= 4: the four 16-bit masks of a row
 // are packed into one 64-bit word, so a warp reads the 16 rows from 32
 // distinct banks. W = 5: one 16-byte row.

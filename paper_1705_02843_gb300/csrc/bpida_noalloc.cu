@@ -75,34 +75,6 @@ unsigned char *g_na_base[NA_MAX_DEVICES] = {};
         }                                                                                         \
     } while (0)
 
-// Manhattan move table (bit 0: move keeps the blank on the board; bit t:
-// tile t moves away from its goal cell).
-MoveLut<4> na_lut()
-{
-    MoveLut<4> L;
-    std::memset(&L, 0, sizeof L);
-    const int W = 4, N = 16;
-    const int dr[4] = {-1, 0, 0, 1}, dc[4] = {0, -1, 1, 0};
-    for (int p = 0; p < N; ++p) {
-        const int r = p / W, c = p % W;
-        for (int m = 0; m < 4; ++m) {
-            const int rr = r + dr[m], cc = c + dc[m];
-            if (rr < 0 || rr >= W || cc < 0 || cc >= W)
-                continue;
-            uint32_t e = 1u;
-            for (int t = 1; t < N; ++t) {
-                const int gr = t / W, gc = t % W;
-                const int before = (rr > gr ? rr - gr : gr - rr) + (cc > gc ? cc - gc : gc - cc);
-                const int after = (r > gr ? r - gr : gr - r) + (c > gc ? c - gc : gc - c);
-                if (after > before)
-                    e |= 1u << t;
-            }
-            L.e[p][m] = e;
-        }
-    }
-    return L;
-}
-
 }  // namespace
 
 extern "C" bpida_status bpida_solve_noalloc(const uint64_t *boards, int n, int *out_len, uint8_t *out_moves,
@@ -174,7 +146,7 @@ extern "C" bpida_status bpida_solve_noalloc(const uint64_t *boards, int n, int *
     d.tune.target_path = NA_TCAP;
     d.tune.growth = 8;
     d.tune.min_pass_ns = 10000;
-    d.lut = na_lut();
+    d.lut = make_move_lut<4>();
     d.graph = 0;
 
     CallDesc desc;

@@ -66,32 +66,6 @@ __global__ void k_pack(const Dev<SV_W> a, Packed *out)
     }
 }
 
-MoveLut<SV_W> sv_lut()
-{
-    MoveLut<SV_W> L;
-    std::memset(&L, 0, sizeof L);
-    const int W = SV_W, N = W * W;
-    const int dr[4] = {-1, 0, 0, 1}, dc[4] = {0, -1, 1, 0};
-    for (int p = 0; p < N; ++p) {
-        const int r = p / W, c = p % W;
-        for (int m = 0; m < 4; ++m) {
-            const int rr = r + dr[m], cc = c + dc[m];
-            if (rr < 0 || rr >= W || cc < 0 || cc >= W)
-                continue;
-            uint32_t e = 1u;
-            for (int t = 1; t < N; ++t) {
-                const int gr = t / W, gc = t % W;
-                const int before = std::abs(rr - gr) + std::abs(cc - gc);
-                const int after = std::abs(r - gr) + std::abs(c - gc);
-                if (after > before)
-                    e |= 1u << t;
-            }
-            L.e[p][m] = e;
-        }
-    }
-    return L;
-}
-
 double now_s()
 {
     using namespace std::chrono;
@@ -382,7 +356,7 @@ bpida_server *bpida_server_create(const bpida_config *cfg, size_t frontier_bytes
     d.tune.target_path = std::min(tcap, 4096);
     d.tune.growth = 8;
     d.tune.min_pass_ns = 10000;
-    d.lut = sv_lut();
+    d.lut = make_move_lut<SV_W>();
     d.graph = 0;
     d.done_list = (unsigned *)(b + o_done);
     sv->d_admit_slot = (unsigned *)(b + o_aslot);

@@ -45,3 +45,19 @@ def test_host_only_calls(lib):
 
 def test_config_struct_layout():
     assert ctypes.sizeof(bpida.Config) == 7 * 4 + 4 + 8 + 16
+
+
+def test_variant_arguments_are_checked_before_any_work(lib):
+    """Unknown variants, and thread-parallel variants (2-4) with a 24-puzzle
+    width, first-solution mode or a node budget, are rejected on the host."""
+    b = bpida.load()
+    bad = [dict(variant=5), dict(variant=-1), dict(variant=bpida.PSIMPLE, width=5),
+           dict(variant=bpida.PSTATICLB, count_all=False), dict(variant=bpida.PFULLLB, node_budget=10)]
+    for kw in bad:
+        width = kw.pop("width", 4)
+        cfg = bpida.make_config(width, **kw)
+        rc = b.bpida_solve_ex(ctypes.byref(cfg), None, 0, None, None, None, None, None, None, None)
+        assert rc == bpida.EINVAL, kw
+    for v in (bpida.PSIMPLE, bpida.PSTATICLB, bpida.PFULLLB):
+        cfg = bpida.make_config(4, variant=v)
+        assert b.bpida_solve_ex(ctypes.byref(cfg), None, 0, None, None, None, None, None, None, None) == bpida.OK

@@ -1,0 +1,259 @@
+"""Thread-parallel IDA* ablations (variants 2-4: PSimple, PStaticLB, PFullLB)
+against the CPU oracle and against an independent model of their load
+balance.
+
+Every integer result must equal the oracle's: status, optimal length, nodes
+expanded in every iteration and the number of optimal solutions. PSimple and
+PStaticLB return the lexicographically first optimal solution (the oracle's);
+PFullLB returns an optimal one, checked by replay. The load-balance figures
+that PSimple and PStaticLB report (largest per-thread node count over the
+mean) are deterministic and are recomputed here in plain Python from the
+root-set rules: breadth-first, in-order partial expansion of nodes with
+f <= limit that are not goals; PStaticLB splits every root whose previous
+load exceeded the per-thread average into at least load / average roots and
+cuts the roots into runs of equal estimated load.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1705_02843_gb300 import bpida
+from paper_1705_02843_gb300 import inputs as I
+from tests import puzzle_ref as P
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+VARIANTS = [bpida.PSIMPLE, bpida.PSTATICLB, bpida.PFULLLB]
+
+
+def tp_solve(W, boards_tiles, variant, threads=0):
+    packed = [I.pack(W, t) for t in boards_tiles]
+    arr = np.array(packed, dtype=np.uint64).reshape(-1)
+    t = torch.from_numpy(arr.view(np.int64)).to("cuda:0")
+    sol = bpida.solve(t, W, bpida.make_config(W, variant=variant, split_target=threads))
+    torch.cuda.synchronize()
+    return sol.status, sol.to_host(), bpida.last_stats()
+
+
+def check(W, tiles, got, ref, variant):
+    for i, (g, r) in enumerate(zip(got, ref)):
+        assert g["status"] == r.status, (i, g["status"], r.status)
+        if r.status != oracle.OK:
+            assert g["length"] == -1
+            continue
+        assert g["length"] == r.length, (i, g["length"], r.length)
+        assert g["nodes"] == r.nodes, (i, g["nodes"], r.nodes)
+        assert g["iters"] == r.iters
+        assert g["solutions"] == r.solutions, (i, g["solutions"], r.solutions)
+        assert len(g["moves"]) == r.length
+        assert P.replay(W, tiles[i], g["moves"]) == list(range(W * W))
+        if variant != bpida.PFULLLB:
+            assert g["moves"] == r.moves, (i, g["moves"], r.moves)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("threads", [0, 128, 1000])
+def test_walks15_match_oracle(variant, threads):
+    tiles = [x.tiles for x in I.walks15_16x40()]
+    rc, got, st = tp_solve(4, tiles, variant, threads)
+    assert rc == bpida.OK
+    check(4, tiles, got, oracle.solve_batch(4, np.array(tiles, dtype=np.uint8)), variant)
+    assert st["tp_threads"] == (threads + 127) // 128 * 128 if threads else st["tp_threads"] > 0
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_edge_cases(variant):
+    goal = list(range(16))
+    one = [1, 0] + list(range(2, 16))
+    walk = I.walks15_16x40()[3].tiles
+    unsolvable = list(walk)
+    a, b = [p for p in range(16) if unsolvable[p]][:2]
+    unsolvable[a], unsolvable[b] = unsolvable[b], unsolvable[a]
+    notperm = [1] * 16
+    tiles = [goal, one, unsolvable, notperm, walk]
+    rc, got, _ = tp_solve(4, tiles, variant)
+    assert rc == bpida.OK  # per-instance outcomes are in the status row
+    assert got[0]["length"] == 0 and got[0]["nodes"] == [1] and got[0]["moves"] == []
+    assert got[1]["length"] == 1 and got[1]["nodes"] == [2] and got[1]["moves"] == [1]
+    for i in (2, 3):
+        assert got[i]["status"] == bpida.EINVAL and got[i]["length"] == -1 and got[i]["nodes"] == []
+    ref = oracle.solve(4, walk)
+    assert got[4]["nodes"] == ref.nodes and got[4]["length"] == ref.length
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_8puzzle_sample(variant):
+    dist, count, order = P.bfs8()
+    rs = np.random.default_rng(5)
+    pick = [order[-1], order[-2]] + [order[i] for i in rs.choice(len(order), 60, replace=False)]
+    tiles = [list(s) for s in pick]
+    rc, got, _ = tp_solve(3, tiles, variant, threads=256)
+    assert rc == bpida.OK
+    ref = oracle.solve_batch(3, np.array(tiles, dtype=np.uint8))
+    check(3, tiles, got, ref, variant)
+    for s, g in zip(pick, got):
+        assert g["length"] == dist[s] and g["solutions"] == count[s]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_permutations_match_golden(variant):
+    """The 12 cheapest boards of the 100-permutation workload (stored oracle
+    results), at the default thread count."""
+    with open(os.path.join(GOLDEN, "perms15_100.json")) as f:
+        gold = {r["index"]: r for r in json.load(f)["instances"]}
+    insts = I.perms15_100()
+    pick = sorted(gold, key=lambda i: sum(gold[i]["nodes"]))[:12]
+    tiles = [insts[i].tiles for i in pick]
+    rc, got, _ = tp_solve(4, tiles, variant)
+    assert rc == bpida.OK
+    for i, g in zip(pick, got):
+        assert g["length"] == gold[i]["length"] and g["nodes"] == gold[i]["nodes"]
+        assert P.replay(4, insts[i].tiles, g["moves"]) == list(range(16))
+        if variant != bpida.PFULLLB:
+            assert "".join(map(str, g["moves"])) == gold[i]["moves"]
+
+
+# ---------------------------------------------------------------------
+# Independent model of PSimple's and PStaticLB's root sets and loads
+# ---------------------------------------------------------------------
+def _children(W, node):
+    s, g, last, h = node
+    out = []
+    for m, c in P.neighbours(W, s):
+        if last is not None and m == 3 - last:
+            continue
+        out.append((c, g + 1, m, P.manhattan_py(W, c)))
+    return out
+
+
+def _expandable(node, L):
+    s, g, last, h = node
+    return h > 0 and g + h <= L and g < 32
+
+
+def _partial_expand(W, nodes, L, target):
+    expanded = 0
+    while len(nodes) < target:
+        need = target - len(nodes)
+        gains = [len(_children(W, n)) - 1 if _expandable(n, L) else 0 for n in nodes]
+        acc, k = 0, None
+        for j, gj in enumerate(gains):
+            if acc < need <= acc + gj:
+                k = j + 1
+                break
+            acc += gj
+        if k is None:
+            k = len(nodes)
+        if sum(gains[:k]) == 0:
+            break
+        new = []
+        for j, n in enumerate(nodes):
+            if j < k and _expandable(n, L):
+                new.extend(_children(W, n))
+                expanded += 1
+            else:
+                new.append(n)
+        nodes = new
+    return nodes, expanded
+
+
+def _pops(W, node, L):
+    """Nodes popped in node's subtree at limit L (sequential IDA* rules)."""
+    s, g, last, h = node
+    if g + h > L:
+        return 0
+    if h == 0:
+        return 1
+    return 1 + sum(_pops(W, c, L) for c in _children(W, node))
+
+
+def _thread_loads(loads, est, T):
+    E = sum(est)
+    P_ = np.concatenate([[0], np.cumsum(est)[:-1]]).astype(object)
+    per = [0] * T
+    j = 0
+    for t in range(T):
+        # roots j with floor(P_j * T / E) == t
+        while j < len(loads) and P_[j] * T < (t + 1) * E:
+            per[t] += loads[j]
+            j += 1
+    return per
+
+
+def _ratio(per, T):
+    tot = sum(per)
+    return float(max(per)) / (float(tot) / float(T)) if tot else 0.0
+
+
+def model(W, tiles, variant, T, n_iters):
+    """Per-iteration (nodes, load ratio) and the final root count."""
+    h0 = P.manhattan_py(W, tiles)
+    start = (tuple(tiles), 0, None, h0)
+    roots, internal = None, 0
+    prev_loads, prev_total, out = None, 0, []
+    for it in range(n_iters):
+        L = h0 + 2 * it
+        if variant == bpida.PSIMPLE or it == 0:
+            roots, ex = _partial_expand(W, [start], L, T)
+            internal = ex if variant == bpida.PSIMPLE else internal + ex
+            est = [1] * len(roots)
+        else:
+            new, est = [], []
+            for r, ld in zip(roots, prev_loads):
+                if prev_total > 0 and ld * T > prev_total and _expandable(r, L):
+                    m = -(-ld * T // prev_total)
+                    sub, ex = _partial_expand(W, [r], L, m)
+                    internal += ex
+                    new.extend(sub)
+                    e = max(1, -(-ld // len(sub)))
+                    est.extend([e] * len(sub))
+                else:
+                    new.append(r)
+                    est.append(max(1, ld))
+            roots = new
+        loads = [_pops(W, r, L) for r in roots]
+        per = _thread_loads(loads, est, T)
+        out.append((internal + sum(loads), _ratio(per, T)))
+        prev_loads, prev_total = loads, sum(loads)
+    return out, len(roots)
+
+
+@pytest.mark.parametrize("variant", [bpida.PSIMPLE, bpida.PSTATICLB])
+@pytest.mark.parametrize("which", [11, 15])
+def test_load_balance_matches_model(variant, which):
+    T = 128
+    tiles = I.walks15_16x40()[which].tiles
+    ref = oracle.solve(4, tiles)
+    rc, got, st = tp_solve(4, [tiles], variant, threads=T)
+    assert rc == bpida.OK and got[0]["nodes"] == ref.nodes
+    per_it, n_roots = model(4, tiles, variant, T, ref.iters)
+    assert [n for n, _ in per_it] == ref.nodes
+    assert st["lb_ratio"] == pytest.approx(per_it[-2][1], rel=1e-12)
+    assert st["lb_ratio_last"] == pytest.approx(per_it[-1][1], rel=1e-12)
+    assert st["tp_roots"] == n_roots
+
+
+def test_full_lb_balances_and_stays_exact():
+    """PFullLB moves work between threads of a block (balancing operations
+    and steals happen) and every count stays exact."""
+    tiles = I.walks15_16x40()[0].tiles
+    rc, got, st = tp_solve(4, [tiles], bpida.PFULLLB, threads=256)
+    assert rc == bpida.OK
+    ref = oracle.solve(4, tiles)
+    assert got[0]["nodes"] == ref.nodes and got[0]["solutions"] == ref.solutions
+    assert st["tp_balances"] > 0 and st["tp_steals"] > 0
+
+
+def test_block_parallel_results_unchanged_after_ablation_calls():
+    tiles = [x.tiles for x in I.walks15_16x40()[:6]]
+    tp_solve(4, tiles, bpida.PFULLLB)
+    packed = np.array([I.pack(4, t) for t in tiles], dtype=np.uint64)
+    sol = bpida.solve(torch.from_numpy(packed.view(np.int64)).cuda(), 4)
+    torch.cuda.synchronize()
+    ref = oracle.solve_batch(4, np.array(tiles, dtype=np.uint8))
+    for g, r in zip(sol.to_host(), ref):
+        assert g["nodes"] == r.nodes and g["moves"] == r.moves
