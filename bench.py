@@ -299,6 +299,65 @@ def run_ablation(args):
                       "results": out}), flush=True)
 
 
+def run_thread_parallel(args):
+    """The paper's thread-parallel configurations (PSimple, PStaticLB,
+    PFullLB: one sequential depth-first search per thread) against this
+    design, one board per solve call on the 100-permutation workload, every
+    result checked against the stored oracle results. Load balance is the
+    paper's maxload / averageload of each board's next-to-last iteration,
+    summarised over the boards whose next-to-last iteration expanded at least
+    10 nodes per search thread."""
+    import torch
+
+    from paper_1705_02843_gb300 import bpida
+
+    torch.cuda.set_device(0)
+    insts = I.WORKLOADS[args.workload]()
+    gold = load_golden(args.workload)
+    b = torch.from_numpy(I.packed_array(insts).view(np.int64)).cuda()
+    stream = torch.cuda.current_stream()
+    names = {bpida.BLOCK_PARALLEL: "this_design", bpida.PSIMPLE: "PSimple", bpida.PSTATICLB: "PStaticLB",
+             bpida.PFULLLB: "PFullLB"}
+    out = {}
+    for v in (bpida.BLOCK_PARALLEL, bpida.PSIMPLE, bpida.PSTATICLB, bpida.PFULLLB):
+        cfg = bpida.make_config(4, variant=v)
+        bpida.solve(b[:1], 4, cfg)  # warm-up (workspace, graphs)
+        torch.cuda.synchronize()
+        ms, ratios, nodes, threads = 0.0, [], 0, 0
+        for i in range(len(insts)):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s = bpida.solve(b[i:i + 1], 4, cfg)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            h = s.to_host()[0]
+            if s.status != bpida.OK or (gold and (h["length"] != gold[i]["length"] or h["nodes"] != gold[i]["nodes"])):
+                raise RuntimeError("%s: board %d differs from the oracle" % (names[v], i))
+            nodes += sum(h["nodes"])
+            st = bpida.last_stats()
+            if v != bpida.BLOCK_PARALLEL:
+                threads = st["tp_threads"]
+                if len(h["nodes"]) >= 2 and h["nodes"][-2] >= 10 * threads:
+                    ratios.append(st["lb_ratio"])
+        row = {"seconds": ms / 1e3, "expansions_per_s": nodes / (ms / 1e3), "instances_per_s": len(insts) / (ms / 1e3)}
+        if v != bpida.BLOCK_PARALLEL:
+            row.update({"threads": threads, "lb_boards": len(ratios),
+                        "lb_mean": statistics.mean(ratios) if ratios else None,
+                        "lb_min": min(ratios) if ratios else None, "lb_max": max(ratios) if ratios else None,
+                        "lb_sd": statistics.pstdev(ratios) if ratios else None})
+        out[names[v]] = row
+        print(json.dumps({names[v]: row}), file=sys.stderr, flush=True)
+    for k in ("PStaticLB", "PFullLB", "this_design"):
+        out[k]["speedup_vs_PSimple"] = out["PSimple"]["seconds"] / out[k]["seconds"]
+    out["this_design"]["speedup_vs_PFullLB"] = out["PFullLB"]["seconds"] / out["this_design"]["seconds"]
+    print(json.dumps({"metric": "ablation: thread-parallel IDA* (PSimple, PStaticLB, PFullLB) vs this design, "
+                                "one board per call, exact results",
+                      "config": {"workload": WORKLOAD_DESC}, "unit": "seconds for all boards", "results": out}),
+          flush=True)
+
+
 def pick_cpu_sample(insts, gold, budget_nodes):
     cores = os.cpu_count() or 1
     if gold:
@@ -325,6 +384,8 @@ def main():
     ap.add_argument("--cpu-sample-nodes", type=float, default=1.5e9)
     ap.add_argument("--ablation", action="store_true",
                     help="compare against the paper's BPIDA* kernel instead")
+    ap.add_argument("--thread-parallel", action="store_true",
+                    help="compare the paper's thread-parallel configurations with this design instead")
     ap.add_argument("--serving", action="store_true",
                     help="run the continuous-batching service under Poisson arrivals instead")
     ap.add_argument("--serving-rates", default="1000,2000,5000,10000,20000,50000")
@@ -351,6 +412,9 @@ def main():
         return
     if args.ablation:
         run_ablation(args)
+        return
+    if args.thread_parallel:
+        run_thread_parallel(args)
         return
 
     import torch

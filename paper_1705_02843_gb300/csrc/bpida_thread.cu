@@ -18,14 +18,19 @@
 //              threads take the shallowest untried branches of busy threads
 //              of the same block through shared memory (DynamicLoadBalance).
 //
-// Root sets are built breadth-first and in order, without duplicate
-// detection: a node is replaced in place by its children (every move but the
-// inverse of the last one, of any f), and only nodes with f <= limit that
-// are not goals are expanded, so the expanded nodes are exactly nodes that
-// sequential IDA* expands at that limit and at every later one. Node counts,
-// lengths and solution counts therefore equal sequential IDA*'s. The load
-// balance of each iteration (the largest per-thread node count over the
-// mean over all threads) is recorded.
+// Root sets are built as the paper's CreateRootSet does, by an A*-style
+// expansion from the start (smallest f first), without duplicate detection:
+// a node is replaced in place by its children (every move but the inverse of
+// the last one), goals are never expanded, and expansion stops once the set
+// holds the wanted number of nodes. The set therefore does not depend on the
+// limit, and PSimple builds it once. The Manhattan distance is consistent
+// (h changes by exactly 1 per move), so f never decreases along a path and
+// sequential IDA* at limit L pops a node exactly when its f <= L: the nodes
+// expanded while building or splitting are kept as a histogram by f, and
+// every iteration counts those with f <= L and takes those with f > L into
+// the next limit. Node counts, lengths and solution counts therefore equal
+// sequential IDA*'s. The load balance of each iteration (the largest
+// per-thread node count over the mean over all threads) is recorded.
 #include "bpida_thread.h"
 #include "bpida_device.cuh"
 
@@ -41,6 +46,7 @@ namespace tp {
 constexpr int TPB = 128;     // threads per search block
 constexpr int PFX = 32;      // moves a root record can carry (2 bits each)
 constexpr int K_CHECK = 64;  // PFullLB: search steps between balancing checks
+constexpr int HF = 128;      // f values of the expanded-node histogram (f = g + h < PFX + 60)
 
 // A root: 24 bytes.
 struct Root {
@@ -60,7 +66,7 @@ struct Ctrl {
     int R;                   // roots in the set
     int fmin_off;            // smallest f - limit over pruned nodes (INT_MAX: none)
     int pad;
-    unsigned long long expanded;  // nodes expanded by the last root-set build or update
+    unsigned long long hist[HF];  // nodes expanded by every build and update so far, by f
     unsigned long long nodes;     // nodes popped by the search threads in this iteration
     unsigned long long maxload;   // largest per-thread count in this iteration
     unsigned long long goals;     // goal nodes popped in this iteration
@@ -109,9 +115,9 @@ template <int W> __device__ __forceinline__ int md(unsigned t, int p)
 
 __device__ __forceinline__ unsigned excl_of(unsigned last) { return last < 4u ? (1u << (3u - last)) : 0u; }
 
-template <int W> __device__ __forceinline__ bool expandable(const Root &r, int L)
+template <int W> __device__ __forceinline__ bool expandable(const Root &r)
 {
-    return r.h > 0 && (int)r.g + (int)r.h <= L && r.g < PFX;
+    return r.h > 0 && r.g < PFX;
 }
 
 template <int W> __device__ __forceinline__ int n_children(const Root &r)
@@ -233,52 +239,63 @@ cudaError_t scan(const unsigned long long *in, unsigned long long *out, int n, u
 // ---------------------------------------------------------------------
 // Root-set construction
 // ---------------------------------------------------------------------
-// Block-wide. Replaces, in place and in order, the first nodes of the list
-// `cur` (cnt nodes) by their children, level after level, until the list
-// holds at least `target` nodes or nothing in it is expandable. `alt` is the
-// other buffer; both hold at least target + 4 nodes. Returns the buffer that
-// holds the result; *expanded gets this thread's share of expanded nodes.
+// Block-wide. Replaces, in place and in order, nodes of the list `cur` (cnt
+// nodes) by their children until the list holds at least `target` nodes or
+// nothing in it is expandable: each step takes the smallest f among the
+// expandable nodes and expands, in list order, the nodes with that f, up to
+// the first prefix of the list whose expansion reaches the target. `alt` is
+// the other buffer; both hold at least target + 4 nodes. Expanded nodes are
+// added to the histogram by f. Returns the buffer that holds the result.
 template <int W>
-__device__ Root *partial_expand(Root *cur, Root *alt, int &cnt, int target, int L, unsigned long long *expanded,
+__device__ Root *partial_expand(Root *cur, Root *alt, int &cnt, int target, unsigned long long *hist,
                                 unsigned long long *ws)
 {
-    __shared__ int s_k;
-    __shared__ unsigned long long s_gk;
-    *expanded = 0;
+    __shared__ int s_k, s_f;
+    __shared__ unsigned s_exp;
     while (cnt < target) {
         const unsigned long long need = (unsigned long long)(target - cnt);
         if (threadIdx.x == 0) {
             s_k = -1;
-            s_gk = 0;
+            s_f = INT_MAX;
+            s_exp = 0;
         }
         __syncthreads();
-        // pass 1: the shortest prefix whose expansion reaches the target
+        // the smallest f among the expandable nodes
+        int fm = INT_MAX;
+        for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+            const Root r = cur[j];
+            if (expandable<W>(r))
+                fm = min(fm, (int)r.g + (int)r.h);
+        }
+        fm = warp_min_int(fm);
+        if ((threadIdx.x & 31) == 0 && fm != INT_MAX)
+            atomicMin(&s_f, fm);
+        __syncthreads();
+        const int fs = s_f;
+        if (fs == INT_MAX)
+            break;
+        // the shortest prefix whose expansion reaches the target
         unsigned long long run = 0;
         for (int base = 0; base < cnt; base += blockDim.x) {
             const int j = base + threadIdx.x;
             unsigned long long gain = 0;
             if (j < cnt) {
                 const Root r = cur[j];
-                if (expandable<W>(r, L))
+                if (expandable<W>(r) && (int)r.g + (int)r.h == fs)
                     gain = (unsigned long long)(n_children<W>(r) - 1);
             }
             unsigned long long tot;
             const unsigned long long ex = block_scan_u64(gain, ws, &tot);
-            if (j < cnt && run + ex < need && run + ex + gain >= need) {
+            if (j < cnt && run + ex < need && run + ex + gain >= need)
                 s_k = j + 1;
-                s_gk = run + ex + gain;
-            }
             run += tot;
             __syncthreads();
             if (s_k >= 0)
                 break;
         }
         const int k = s_k >= 0 ? s_k : cnt;
-        const unsigned long long gk = s_k >= 0 ? s_gk : run;
         __syncthreads();
-        if (gk == 0)
-            break;
-        // pass 2: write the new list
+        // write the new list
         unsigned long long run2 = 0;
         for (int base = 0; base < cnt; base += blockDim.x) {
             const int j = base + threadIdx.x;
@@ -291,7 +308,7 @@ __device__ Root *partial_expand(Root *cur, Root *alt, int &cnt, int target, int 
             unsigned long long gain = 0;
             if (j < cnt) {
                 r = cur[j];
-                ex_j = j < k && expandable<W>(r, L);
+                ex_j = j < k && expandable<W>(r) && (int)r.g + (int)r.h == fs;
                 if (ex_j)
                     gain = (unsigned long long)(n_children<W>(r) - 1);
             }
@@ -304,25 +321,27 @@ __device__ Root *partial_expand(Root *cur, Root *alt, int &cnt, int target, int 
                     for (int m = 0; m < 4; ++m)
                         if ((allow >> m) & 1u)
                             alt[pos++] = child_of<W>(r, m);
-                    *expanded += 1;
+                    atomicAdd(&s_exp, 1u);
                 } else {
                     alt[pos] = r;
                 }
             }
             run2 += tot;
         }
-        cnt += (int)gk;
+        cnt += (int)run2;
         Root *t = cur;
         cur = alt;
         alt = t;
         __syncthreads();
+        if (threadIdx.x == 0 && s_exp)
+            atomicAdd(&hist[fs], (unsigned long long)s_exp);
     }
     return cur;
 }
 
-// PSimple's root set (and every variant's first one): about T roots from
-// the start at limit L. One block.
-template <int W> __global__ void __launch_bounds__(1024) k_build(const Args<W> a, int L, int target)
+// The root set of every variant's first iteration (PSimple keeps it): about
+// T roots from the start. One block.
+template <int W> __global__ void __launch_bounds__(1024) k_build(const Args<W> a, int target)
 {
     __shared__ unsigned long long ws[32];
     Ctrl *c = a.ctrl;
@@ -339,15 +358,12 @@ template <int W> __global__ void __launch_bounds__(1024) k_build(const Args<W> a
     }
     __syncthreads();
     int cnt = 1;
-    unsigned long long ex = 0;
-    Root *res = partial_expand<W>(a.A, a.B, cnt, target, L, &ex, ws);
+    Root *res = partial_expand<W>(a.A, a.B, cnt, target, c->hist, ws);
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
         if (res != a.A)
             a.A[j] = res[j];
         a.est[j] = 1ull;
     }
-    if (ex)
-        atomicAdd(&c->expanded, ex);
     if (threadIdx.x == 0)
         c->R = cnt;
 }
@@ -356,14 +372,14 @@ template <int W> __global__ void __launch_bounds__(1024) k_build(const Args<W> a
 // is split when its load exceeds the per-thread average prev / T (prev: the
 // nodes the threads popped in the previous iteration), into at least
 // ceil(load / average) roots.
-template <int W> __global__ void k_mark(const Args<W> a, int R, int L, unsigned long long prev)
+template <int W> __global__ void k_mark(const Args<W> a, int R, unsigned long long prev)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= R)
         return;
     const unsigned long long ld = a.load[j];
     const unsigned long long T = (unsigned long long)a.T;
-    const bool heavy = prev > 0 && ld * T > prev && expandable<W>(a.A[j], L);
+    const bool heavy = prev > 0 && ld * T > prev && expandable<W>(a.A[j]);
     const unsigned long long m = heavy ? (ld * T + prev - 1) / prev : 0ull;
     a.want[j] = m;
     a.soff[j] = heavy ? 2 * (m + 4) : 0ull;
@@ -377,9 +393,9 @@ template <int W> __global__ void k_heavy_index(const Args<W> a, int R)
         a.heavy[a.hpos[j]] = (unsigned)j;
 }
 
-// Step 2: one block per root to split; partial breadth-first expansion in
-// the root's own scratch region (two halves of want + 4 nodes).
-template <int W> __global__ void __launch_bounds__(TPB) k_split_heavy(const Args<W> a, int L)
+// Step 2: one block per root to split, expanded smallest f first in the
+// root's own scratch region (two halves of want + 4 nodes).
+template <int W> __global__ void __launch_bounds__(TPB) k_split_heavy(const Args<W> a)
 {
     __shared__ unsigned long long ws[32];
     const unsigned j = a.heavy[blockIdx.x];
@@ -390,13 +406,10 @@ template <int W> __global__ void __launch_bounds__(TPB) k_split_heavy(const Args
         cur[0] = a.A[j];
     __syncthreads();
     int cnt = 1;
-    unsigned long long ex = 0;
-    Root *res = partial_expand<W>(cur, alt, cnt, m, L, &ex, ws);
+    Root *res = partial_expand<W>(cur, alt, cnt, m, a.ctrl->hist, ws);
     if (res != cur)
         for (int q = threadIdx.x; q < cnt; q += blockDim.x)
             cur[q] = res[q];
-    if (ex)
-        atomicAdd(&a.ctrl->expanded, ex);
     if (threadIdx.x == 0)
         a.cntv[j] = (unsigned long long)cnt;
 }
@@ -783,7 +796,6 @@ template <int W> __global__ void k_init(const Args<W> a, const uint64_t *boards,
 template <int W> __global__ void k_reset_iter(const Args<W> a)
 {
     Ctrl *c = a.ctrl;
-    c->expanded = 0;
     c->nodes = 0;
     c->maxload = 0;
     c->goals = 0;
@@ -906,41 +918,41 @@ bpida_status solve_one(const Settings &cfg, Workspace &ws, Args<W> a, const uint
         return finish(BPIDA_ELIMIT, -1, 0);
 
     int L = hc.h0, it = 0, R = 0;
-    unsigned long long internal = 0, prev = 0;
+    unsigned long long prev = 0;
     std::vector<double> ratio;
     for (;;) {
         k_reset_iter<W><<<1, 1, 0, st>>>(a);
         TK(cudaGetLastError());
-        bool built = false;
-        if (cfg.variant == PSIMPLE || it == 0) {
-            k_build<W><<<1, 1024, 0, st>>>(a, L, std::min(T, Rcap - 4));
+        stats->launches += 1;
+        if (it == 0) {
+            // CreateRootSet (PSimple keeps this set in every iteration)
+            k_build<W><<<1, 1024, 0, st>>>(a, std::min(T, Rcap - 4));
             TK(cudaGetLastError());
             TK(fetch());
             R = hc.R;
-            internal = (cfg.variant == PSIMPLE ? 0ull : internal) + hc.expanded;
-            stats->launches += 2;
-            built = true;
-        }
-        if (!built) {
+            stats->launches += 1;
+        } else if (cfg.variant != PSIMPLE) {
             // UpdateRootSet: split the roots that took more than the average
             const int gb = (R + th - 1) / th;
-            k_mark<W><<<gb, th, 0, st>>>(a, R, L, prev);
+            k_mark<W><<<gb, th, 0, st>>>(a, R, prev);
             TK(cudaGetLastError());
             TK(scan(a.soff, a.soff, R, a.bsum, &a.ctrl->tot[0], st));
             TK(scan(a.hpos, a.hpos, R, a.bsum, &a.ctrl->tot[1], st));
             TK(fetch());
             const unsigned long long S_tot = hc.tot[0], H = hc.tot[1];
             stats->launches += 7;
+            // fewer than T roots can take more than the average, so the
+            // split regions (2 * (want + 4) nodes each) always fit in Scap;
+            // the set itself may reach Rcap, and is then kept as it is
             const bool fits = H > 0 && S_tot <= Scap && (unsigned long long)R + S_tot / 2 <= (unsigned long long)Rcap;
             if (fits) {
                 k_heavy_index<W><<<gb, th, 0, st>>>(a, R);
-                k_split_heavy<W><<<(unsigned)H, TPB, 0, st>>>(a, L);
+                k_split_heavy<W><<<(unsigned)H, TPB, 0, st>>>(a);
                 k_counts<W><<<gb, th, 0, st>>>(a, R);
                 TK(cudaGetLastError());
                 TK(scan(a.npos, a.npos, R, a.bsum, &a.ctrl->tot[2], st));
                 TK(fetch());
                 const int Rn = (int)hc.tot[2];
-                internal += hc.expanded;
                 k_compose<W><<<gb, th, 0, st>>>(a, R);
                 TK(cudaGetLastError());
                 std::swap(a.A, a.B);
@@ -951,6 +963,15 @@ bpida_status solve_one(const Settings &cfg, Workspace &ws, Args<W> a, const uint
                 TK(cudaGetLastError());
                 stats->launches += 1;
             }
+        }
+        // expanded nodes popped at this limit, and the smallest f above it
+        unsigned long long internal = 0;
+        int hist_off = INT_MAX;
+        for (int f = 0; f < HF; ++f) {
+            if (f <= L)
+                internal += hc.hist[f];
+            else if (hc.hist[f] && hist_off == INT_MAX)
+                hist_off = f - L;
         }
         // assignment: prefix sums of the estimates
         TK(scan(a.est, a.P, R, a.bsum, &a.ctrl->tot[3], st));
@@ -975,11 +996,12 @@ bpida_status solve_one(const Settings &cfg, Workspace &ws, Args<W> a, const uint
         stats->steps += 1;
         if (hc.goals > 0)
             return finish(BPIDA_OK, L, it + 1);
-        if (hc.fmin_off == INT_MAX || hc.fmin_off <= 0)
+        const int off = std::min(hc.fmin_off, hist_off);
+        if (off == INT_MAX || off <= 0)
             return finish(BPIDA_EINTERNAL, -1, it + 1);
-        if (it + 1 >= MAXIT || L + hc.fmin_off > MAXLEN)
+        if (it + 1 >= MAXIT || L + off > MAXLEN)
             return finish(BPIDA_ELIMIT, -1, it + 1);
-        L += hc.fmin_off;
+        L += off;
         ++it;
         prev = hc.nodes;
     }
@@ -1007,11 +1029,11 @@ bpida_status solve_wd(const Settings &cfg, const uint64_t *boards, int n, int *o
         return BPIDA_EINVAL;
     const int grid = cfg.threads > 0 ? (cfg.threads + TPB - 1) / TPB : sms * bpsm;
     const int T = grid * TPB;
-    const long long rcap = (long long)(cfg.variant == PSIMPLE ? 2 : 16) * T + 4096;
+    const long long rcap = (long long)(cfg.variant == PSIMPLE ? 2 : 32) * T + 4096;
     if (rcap > (1ll << 30))
         return BPIDA_ENOMEM;
     const int Rcap = (int)rcap;
-    const size_t Scap = (size_t)4 * T + 4096;
+    const size_t Scap = (size_t)12 * T + 4096;
     const size_t u64 = sizeof(unsigned long long);
 
     TK(ws.ensure(ws.ctrl, sizeof(Ctrl)));

@@ -8,10 +8,11 @@ PStaticLB return the lexicographically first optimal solution (the oracle's);
 PFullLB returns an optimal one, checked by replay. The load-balance figures
 that PSimple and PStaticLB report (largest per-thread node count over the
 mean) are deterministic and are recomputed here in plain Python from the
-root-set rules: breadth-first, in-order partial expansion of nodes with
-f <= limit that are not goals; PStaticLB splits every root whose previous
-load exceeded the per-thread average into at least load / average roots and
-cuts the roots into runs of equal estimated load.
+root-set rules: in-order expansion of the nodes with the smallest f (goals
+are never expanded) until the set holds the wanted number of nodes; PStaticLB
+splits every root whose previous load exceeded the per-thread average into
+at least load / average roots the same way and cuts the roots into runs of
+equal estimated load.
 """
 import json
 import os
@@ -130,16 +131,21 @@ def _children(W, node):
     return out
 
 
-def _expandable(node, L):
+def _expandable(node):
     s, g, last, h = node
-    return h > 0 and g + h <= L and g < 32
+    return h > 0 and g < 32
 
 
-def _partial_expand(W, nodes, L, target):
-    expanded = 0
+def _partial_expand(W, nodes, target, hist):
+    """Smallest f first, in list order, until the list holds target nodes;
+    expanded nodes are counted in hist by f."""
     while len(nodes) < target:
+        cand = [n[1] + n[3] for n in nodes if _expandable(n)]
+        if not cand:
+            break
+        fs = min(cand)
         need = target - len(nodes)
-        gains = [len(_children(W, n)) - 1 if _expandable(n, L) else 0 for n in nodes]
+        gains = [len(_children(W, n)) - 1 if _expandable(n) and n[1] + n[3] == fs else 0 for n in nodes]
         acc, k = 0, None
         for j, gj in enumerate(gains):
             if acc < need <= acc + gj:
@@ -148,17 +154,15 @@ def _partial_expand(W, nodes, L, target):
             acc += gj
         if k is None:
             k = len(nodes)
-        if sum(gains[:k]) == 0:
-            break
         new = []
         for j, n in enumerate(nodes):
-            if j < k and _expandable(n, L):
+            if j < k and _expandable(n) and n[1] + n[3] == fs:
                 new.extend(_children(W, n))
-                expanded += 1
+                hist[fs] = hist.get(fs, 0) + 1
             else:
                 new.append(n)
         nodes = new
-    return nodes, expanded
+    return nodes
 
 
 def _pops(W, node, L):
@@ -190,24 +194,23 @@ def _ratio(per, T):
 
 
 def model(W, tiles, variant, T, n_iters):
-    """Per-iteration (nodes, load ratio) and the final root count."""
+    """Per-iteration (nodes, load ratio) and the final root count. The
+    expanded nodes are counted at a limit L when their f <= L (f never
+    decreases along a path under the Manhattan distance)."""
     h0 = P.manhattan_py(W, tiles)
     start = (tuple(tiles), 0, None, h0)
-    roots, internal = None, 0
+    hist = {}
+    roots = _partial_expand(W, [start], T, hist)
+    est = [1] * len(roots)
     prev_loads, prev_total, out = None, 0, []
     for it in range(n_iters):
         L = h0 + 2 * it
-        if variant == bpida.PSIMPLE or it == 0:
-            roots, ex = _partial_expand(W, [start], L, T)
-            internal = ex if variant == bpida.PSIMPLE else internal + ex
-            est = [1] * len(roots)
-        else:
+        if it > 0 and variant == bpida.PSTATICLB:
             new, est = [], []
             for r, ld in zip(roots, prev_loads):
-                if prev_total > 0 and ld * T > prev_total and _expandable(r, L):
+                if prev_total > 0 and ld * T > prev_total and _expandable(r):
                     m = -(-ld * T // prev_total)
-                    sub, ex = _partial_expand(W, [r], L, m)
-                    internal += ex
+                    sub = _partial_expand(W, [r], m, hist)
                     new.extend(sub)
                     e = max(1, -(-ld // len(sub)))
                     est.extend([e] * len(sub))
@@ -217,6 +220,7 @@ def model(W, tiles, variant, T, n_iters):
             roots = new
         loads = [_pops(W, r, L) for r in roots]
         per = _thread_loads(loads, est, T)
+        internal = sum(c for f, c in hist.items() if f <= L)
         out.append((internal + sum(loads), _ratio(per, T)))
         prev_loads, prev_total = loads, sum(loads)
     return out, len(roots)
