@@ -53,13 +53,13 @@ WORKLOAD_DESC = ("perms15_100: 100 seeded uniformly random solvable 15-puzzle bo
 # state (the work the method needs per expansion), from ncu
 # (smsp__inst_executed.sum / nodes) on the final iteration of board 0 run as
 # one pass: profiles/k_search_15puzzle_perms15_board0_final_iteration.txt.
-INSTR_PER_EXPANSION = 5.49
+INSTR_PER_EXPANSION = 5.53
 # The same ratio over every k_search launch of a plain solve of board 0
 # (hand-back on, as in the benchmark): ramp-up, short passes and hand-back
 # copies included. profiles/k_search_15puzzle_plain_solve_all_launches.txt.
-INSTR_PER_EXPANSION_PLAIN_MIX = 7.18
+INSTR_PER_EXPANSION_PLAIN_MIX = 7.27
 # DRAM bytes (read + write) per k_search launch over those launches.
-TRAFFIC_PER_LAUNCH = 1230571
+TRAFFIC_PER_LAUNCH = 1233726
 
 
 def golden_path(name):
@@ -400,6 +400,9 @@ def main():
                          "k_search launch is number iters-1), print its statistics and exit")
     ap.add_argument("--profile-default", action="store_true",
                     help="with --profile-case: keep the default hand-back (as in the bench)")
+    ap.add_argument("--profile-variant", type=int, default=0, metavar="V",
+                    help="with --profile-case: solve with bpida_config.variant V (2-4: the thread-parallel "
+                         "configurations; the final iteration's k_search_tp launch is number iters-1)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local = dist_setup()
@@ -437,8 +440,12 @@ def main():
         for rep in range(2):
             # host-driven loop: ncu cannot see kernels inside graphs that
             # hold conditional nodes
-            s = bpida.solve(b, 4, bpida.make_config(4, exit_fraction_pct=0 if args.profile_default else 100,
-                                                    driver=1))
+            if args.profile_variant >= 2:
+                cfg = bpida.make_config(4, variant=args.profile_variant)
+            else:
+                cfg = bpida.make_config(4, exit_fraction_pct=0 if args.profile_default else 100, driver=1,
+                                        variant=args.profile_variant)
+            s = bpida.solve(b, 4, cfg)
             torch.cuda.synchronize(dev)
         h = s.to_host()[0]
         st = bpida.last_stats()
