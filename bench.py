@@ -358,6 +358,86 @@ def run_thread_parallel(args):
           flush=True)
 
 
+def run_workloads(args):
+    """The other workloads: the 4096-board mix (95% random walks of 20-90
+    moves, 5% random permutations) solved in one batched call and one board
+    per call, and the 1024 24-puzzle walks (40-100 moves) batched with the
+    oracle's node budget of 5e7 nodes per board. Every result is checked
+    against the stored oracle results. Expansions count the nodes of the
+    iterations each board completed."""
+    import torch
+
+    from paper_1705_02843_gb300 import bpida
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / 1e3
+
+    def check(name, gold, hosts, idx):
+        # a board stopped by the node budget reports its completed
+        # iterations; the stored oracle row also holds the partial last one
+        for i, h in zip(idx, hosts):
+            g = gold[i]
+            want = g["nodes"] if g["status"] == 0 else g["nodes"][:-1]
+            if h["status"] != g["status"] or h["nodes"] != want or (
+                    g["status"] == 0 and (h["length"] != g["length"] or "".join(map(str, h["moves"])) != g["moves"])):
+                raise RuntimeError("%s: board %d differs from the oracle" % (name, i))
+        return sum(sum(h["nodes"]) for h in hosts)
+
+    out = {}
+    # 15-puzzle mix: batched and plain
+    insts = I.mixed15_4096()
+    gold = load_golden("mixed15_4096")
+    n = len(insts)
+    b = torch.from_numpy(I.packed_array(insts).view(np.int64)).cuda()
+    cfg = bpida.make_config(4)
+    bpida.solve(b, 4, cfg)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(max(1, args.steps)):
+        sol, t = timed(lambda: bpida.solve(b, 4, cfg))
+        ts.append(t)
+    nodes = check("mixed15_4096 batched", gold, sol.to_host(), range(n))
+    t_b = statistics.median(ts)
+    sols, t_p = timed(lambda: [bpida.solve(b[i:i + 1], 4, cfg) for i in range(n)])
+    check("mixed15_4096 plain", gold, [s.to_host()[0] for s in sols], range(n))
+    out["mixed15_4096"] = {"boards": n, "expansions": nodes,
+                           "batched": {"seconds": t_b, "expansions_per_s": nodes / t_b, "instances_per_s": n / t_b},
+                           "plain": {"seconds": t_p, "expansions_per_s": nodes / t_p, "instances_per_s": n / t_p},
+                           "batched_over_plain_instances_per_s": t_p / t_b}
+    print(json.dumps({"mixed15_4096": out["mixed15_4096"]}), file=sys.stderr, flush=True)
+    # 24-puzzle walks with the oracle's node budget
+    insts = I.walks24_1024()
+    gold = load_golden("walks24_1024")
+    n = len(insts)
+    b = torch.from_numpy(I.packed_array(insts).view(np.int64).reshape(n, 2)).cuda()
+    cfg = bpida.make_config(5, node_budget=50_000_000)
+    bpida.solve(b, 5, cfg)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(max(1, args.steps)):
+        sol, t = timed(lambda: bpida.solve(b, 5, cfg))
+        ts.append(t)
+    hosts = sol.to_host()
+    nodes = check("walks24_1024", gold, hosts, range(n))
+    t_b = statistics.median(ts)
+    solved = sum(1 for h in hosts if h["status"] == 0)
+    out["walks24_1024"] = {"boards": n, "solved_within_budget": solved, "node_budget": 50_000_000,
+                           "expansions": nodes, "seconds": t_b, "expansions_per_s": nodes / t_b,
+                           "instances_per_s": n / t_b}
+    print(json.dumps({"walks24_1024": out["walks24_1024"]}), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "15-puzzle mix and 24-puzzle walks: expansions/s and instances/s, oracle-exact",
+                      "data": "synthetic", "results": out}), flush=True)
+
+
 def pick_cpu_sample(insts, gold, budget_nodes):
     cores = os.cpu_count() or 1
     if gold:
@@ -384,6 +464,8 @@ def main():
     ap.add_argument("--cpu-sample-nodes", type=float, default=1.5e9)
     ap.add_argument("--ablation", action="store_true",
                     help="compare against the paper's BPIDA* kernel instead")
+    ap.add_argument("--workloads", action="store_true",
+                    help="measure the 4096-board mix (batched and plain) and the 24-puzzle walks instead")
     ap.add_argument("--thread-parallel", action="store_true",
                     help="compare the paper's thread-parallel configurations with this design instead")
     ap.add_argument("--serving", action="store_true",
@@ -418,6 +500,9 @@ def main():
         return
     if args.thread_parallel:
         run_thread_parallel(args)
+        return
+    if args.workloads:
+        run_workloads(args)
         return
 
     import torch
