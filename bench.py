@@ -210,7 +210,7 @@ def run_serving(args):
         stream = I.serving_stream(rate, n_req, seed=300000 + int(rate))
         words = [int(w) for w in I.packed_array([x for _, x in stream])]
         lat, t_first, t_last = [], None, None
-        with bpida.Server(frontier_bytes=2 << 30, max_slots=8192) as sv:
+        with bpida.Server(frontier_bytes=2 << 30, max_slots=8192, time_slice_us=args.serving_slice_us) as sv:
             t0 = bpida.Server.clock()
             i = 0
             got = 0
@@ -235,12 +235,15 @@ def run_serving(args):
         lat.sort()
         out.append({"rate_per_s": rate, "requests": n_req, "completed_per_s": n_req / t_end,
                     "p50_ms": 1e3 * lat[len(lat) // 2], "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                    "device_steps": st["steps"], "max_active": st["max_active"], "wall_s": t_end})
+                    "device_steps": st["steps"], "sliced_steps": st["sliced_steps"], "max_active": st["max_active"],
+                    "wall_s": t_end})
         print(json.dumps(out[-1]), file=sys.stderr, flush=True)
     print(json.dumps({"metric": "15-puzzle serving: completed requests/s and p50/p99 latency (submit to result)",
                       "unit": "requests/s", "data": "synthetic",
                       "config": {"workload": "Poisson arrivals; 98% walks of 30-90 moves, 2% random permutations",
-                                 "slots": 8192, "mode": "continuous batching"},
+                                 "slots": 8192, "mode": "continuous batching",
+                                 "time_slice_us": args.serving_slice_us if args.serving_slice_us is not None
+                                 else "library default (2000)"},
                       "rates": out}), flush=True)
 
 
@@ -473,6 +476,8 @@ def main():
     ap.add_argument("--serving-rates", default="1000,2000,5000,10000,20000,50000")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--serving-max-requests", type=int, default=20000)
+    ap.add_argument("--serving-slice-us", type=int, default=None,
+                    help="time slice of a device step in microseconds (0 = none; default: the library's)")
     ap.add_argument("--driver", default="graph", choices=["graph", "host"],
                     help="graph: each solve call is one CUDA graph launch (default); host: the "
                          "host launches every kernel (same kernels; ncu can list them)")

@@ -246,6 +246,8 @@ typedef struct {
     int max_active;             /* most instances searched in one step */
     uint64_t submitted, admitted, completed;
     uint64_t steps, passes;     /* device threshold steps and search passes */
+    uint64_t sliced_steps;      /* steps cut by the time slice (open nodes
+                                   carried into the next step) */
 } bpida_server_stats;
 
 /* Create a server on the current device. cfg may be NULL (width must be 4;
@@ -264,6 +266,13 @@ int bpida_server_in_flight(bpida_server *sv);
 void bpida_server_get_stats(bpida_server *sv, bpida_server_stats *out);
 /* The clock used for submit_time_s / done_time_s (seconds, monotonic). */
 double bpida_server_clock(void);
+/* Time slice of a device step (default 2000 microseconds; 0 = none). When a
+ * step has searched for this long it stops, and every iteration it did not
+ * finish continues in the next step from its open nodes, so requests with
+ * short iterations finish (and new ones are admitted) without waiting for
+ * the longest iteration on the GPU. Results do not depend on it. Takes
+ * effect from the next step. */
+void bpida_server_set_time_slice(bpida_server *sv, int microseconds);
 /* Stop the service (pending requests are dropped) and free it. */
 void bpida_server_destroy(bpida_server *sv);
 

@@ -24,7 +24,7 @@ EXPORTS = (
     "bpida_max_len", "bpida_max_iters", "bpida_solve", "bpida_solve_ex", "bpida_set_timing",
     "bpida_get_stats", "bpida_release_workspace", "bpida_status_str", "bpida_solve_noalloc",
     "bpida_server_create", "bpida_server_submit", "bpida_server_poll", "bpida_server_in_flight",
-    "bpida_server_get_stats", "bpida_server_clock", "bpida_server_destroy",
+    "bpida_server_get_stats", "bpida_server_clock", "bpida_server_set_time_slice", "bpida_server_destroy",
 )
 NOALLOC_MAX_BOARDS = 256
 
@@ -106,6 +106,7 @@ class ServerStats(ctypes.Structure):
         ("completed", ctypes.c_uint64),
         ("steps", ctypes.c_uint64),
         ("passes", ctypes.c_uint64),
+        ("sliced_steps", ctypes.c_uint64),
     ]
 
     def as_dict(self):
@@ -152,6 +153,8 @@ def load():
         lib.bpida_server_get_stats.restype = None
         lib.bpida_server_clock.argtypes = []
         lib.bpida_server_clock.restype = ctypes.c_double
+        lib.bpida_server_set_time_slice.argtypes = [vp, ctypes.c_int]
+        lib.bpida_server_set_time_slice.restype = None
         lib.bpida_server_destroy.argtypes = [vp]
         lib.bpida_server_destroy.restype = None
         lib.bpida_status_str.argtypes = [ctypes.c_int]
@@ -303,13 +306,15 @@ class Server:
     """Continuous-batching 15-puzzle solve service (bpida_server_* calls)."""
 
     def __init__(self, frontier_bytes: int = 1 << 30, max_slots: int = 4096,
-                 config: Optional[Config] = None):
+                 config: Optional[Config] = None, time_slice_us: Optional[int] = None):
         lib = load()
         cfg = config if config is not None else make_config(4)
         self._lib = lib
         self._h = lib.bpida_server_create(ctypes.byref(cfg), frontier_bytes, max_slots)
         if not self._h:
             raise RuntimeError("bpida_server_create failed")
+        if time_slice_us is not None:
+            lib.bpida_server_set_time_slice(self._h, time_slice_us)
         self._buf = (Result * 256)()
 
     def submit(self, packed_board: int, req_id: int) -> None:

@@ -196,6 +196,10 @@ struct Ctrl {
     int first_pass;   // 1: this pass reads the splitter's frontiers in place
     int done_warps;   // search blocks finished in this pass (one warp each in the paper kernel)
     int done_blocks;  // blocks finished in the current split / advance / init
+    int n_front;      // records of this step's frontiers (the first pass's input starts with them)
+    int n_carry;      // serving: open nodes carried over from the previous step
+    int carry_q;      // serving: the queue that holds them
+    unsigned long long step_t0;  // start of this step (%globaltimer)
     int n_done;       // serving: entries of the done list
     unsigned long long records_total;
     unsigned long long handed_back_total;
@@ -266,6 +270,7 @@ struct Tune {
     int target_path;     // frontier records wanted for a path step
     int growth;          // expected node growth per iteration (x)
     int min_pass_ns;     // a pass hands work back only after running this long
+    unsigned long long step_ns;  // serving: time slice of a step (0 = none)
 };
 
 // ---------------------------------------------------------------------
@@ -342,7 +347,30 @@ template <int W> struct Dev {
     unsigned *done_list;        // serving: instances that finished in this step (else null)
     unsigned char *ovf;         // per-warp overflow stacks in global memory (may be null)
     int ovf_cap;                // entries per warp overflow stack (0 = none)
+    // Serving with time slices (slice = 1): an instance's iteration may run
+    // over several steps. Frontier regions then belong to instance slots, not
+    // to positions in the active list; carry[i] = 1 marks a slot whose open
+    // nodes were carried into the next step (no split, no advance), and
+    // fbase[i] / fcount[i] locate the frontier of its current iteration.
+    int slice;
+    unsigned *carry;
+    int *fbase, *fcount;
 };
+
+__device__ __forceinline__ unsigned long long global_ns();
+
+// Frontier region of the problem at active position k (instance inst).
+template <int W> __device__ __forceinline__ size_t region_of(const Dev<W> &a, int k, unsigned inst)
+{
+    return (size_t)(a.slice ? (int)inst : k) * 2 * (size_t)a.C;
+}
+
+// The step's time slice is over (serving).
+template <int W> __device__ __forceinline__ bool slice_over(const Dev<W> &a)
+{
+    return a.slice && a.tune.step_ns &&
+           global_ns() - *(volatile unsigned long long *)&a.ctrl->step_t0 > a.tune.step_ns;
+}
 
 __device__ __forceinline__ unsigned long long global_ns()
 {
@@ -523,11 +551,19 @@ __device__ __forceinline__ void hand_back_stack(const Dev<W> &a, Rec<W> *out, co
 // per-problem frontiers in place: problem k owns indices
 // [offset[k], offset[k] + count[k]); the origin of a frontier record is its
 // index. Later passes read the hand-back queue.
+// Input record idx of a pass. The first pass of a step reads the frontiers
+// in place (indices below n_front; problem k owns [offset[k], offset[k] +
+// count[k]), and a frontier record's origin is its index), then the open
+// nodes carried over from the previous step (serving), which sit in `in`.
+// Later passes read the hand-back queue `in`.
 template <int W>
-__device__ __forceinline__ Rec<W> load_rec(const Dev<W> &a, bool frontier, int n_active, const Rec<W> *in, int idx)
+__device__ __forceinline__ Rec<W> load_rec(const Dev<W> &a, bool frontier, int n_active, int n_front,
+                                           const unsigned *act, const Rec<W> *in, int idx)
 {
     if (!frontier)
         return in[idx];
+    if (idx >= n_front)
+        return in[idx - n_front];
     int lo = 0, hi = n_active - 1;  // last k with offset[k] <= idx
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -536,14 +572,15 @@ __device__ __forceinline__ Rec<W> load_rec(const Dev<W> &a, bool frontier, int n
         else
             hi = mid - 1;
     }
-    Rec<W> r = a.scratch[(size_t)lo * 2 * a.C + (idx - a.offset[lo])];
+    Rec<W> r = a.scratch[region_of(a, lo, a.slice ? act[lo] : 0u) + (idx - a.offset[lo])];
     r.origin = (uint32_t)idx;
     return r;
 }
 
 template <int W>
-__device__ __forceinline__ void hand_back_records(const Dev<W> &a, bool frontier, int n_active, const Rec<W> *in,
-                                                  Rec<W> *out, int from, int to, int lane)
+__device__ __forceinline__ void hand_back_records(const Dev<W> &a, bool frontier, int n_active, int n_front,
+                                                  const unsigned *act, const Rec<W> *in, Rec<W> *out, int from,
+                                                  int to, int lane)
 {
     const int k = to - from;
     if (k <= 0)
@@ -558,7 +595,7 @@ __device__ __forceinline__ void hand_back_records(const Dev<W> &a, bool frontier
         return;
     }
     for (int j = lane; j < k; j += 32)
-        out[base + j] = load_rec<W>(a, frontier, n_active, in, from + j);
+        out[base + j] = load_rec<W>(a, frontier, n_active, n_front, act, in, from + j);
 }
 
 template <int W> __device__ void end_of_pass(const Dev<W> &a);
@@ -593,6 +630,8 @@ __global__ void k_search(const Dev<W> a)
     Rec<W> *out = a.ctrl->qi ? a.q0 : a.q1;
     const bool frontier = a.ctrl->first_pass != 0;
     const int n_act = a.ctrl->n_active;
+    const int n_front = a.ctrl->n_front;
+    const unsigned *act = a.ctrl->cur ? a.act1 : a.act0;
     const bool first_only = a.desc->first_only != 0;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -647,7 +686,7 @@ __global__ void k_search(const Dev<W> a)
             const bool v = idx < end;
             Rec<W> r;
             if (v)
-                r = load_rec<W>(a, frontier, n_act, in, idx);
+                r = load_rec<W>(a, frontier, n_act, n_front, act, in, idx);
             const unsigned inst = v ? r.inst : 0xffffffffu;
             const unsigned inst0 = __shfl_sync(FULL, inst, 0);
             const unsigned same = __ballot_sync(FULL, v && inst == inst0);
@@ -805,6 +844,9 @@ __global__ void k_search(const Dev<W> a)
                         if (lane == 0 && *(volatile int *)&a.ctrl->exited >= a.tune.exit_threshold)
                             go = global_ns() - *(volatile unsigned long long *)&a.ctrl->t_start >=
                                  (unsigned long long)a.tune.min_pass_ns;
+                        // serving: the step's time slice is over
+                        if (lane == 0 && !go && slice_over(a))
+                            go = 1;
                         if (__shfl_sync(FULL, go, 0)) {
                             stop = true;
                             break;
@@ -822,7 +864,19 @@ __global__ void k_search(const Dev<W> a)
                 if (OVF)
                     hand_back_stack<W, S>(a, out, ovf, 0, ovf_n, inst0, lane);
                 ovf_n = 0;
-                hand_back_records<W>(a, frontier, n_act, in, out, i + cnt, end, lane);
+                hand_back_records<W>(a, frontier, n_act, n_front, act, in, out, i + cnt, end, lane);
+                // input that no warp has taken yet goes back too (a stop at
+                // the end of a serving time slice can come before the input
+                // is exhausted; otherwise nothing is left here)
+                for (;;) {
+                    int h2 = 0;
+                    if (lane == 0)
+                        h2 = atomicAdd(&a.ctrl->head, chunk);
+                    h2 = __shfl_sync(FULL, h2, 0);
+                    if (h2 >= n_in)
+                        break;
+                    hand_back_records<W>(a, frontier, n_act, n_front, act, in, out, h2, min(h2 + chunk, n_in), lane);
+                }
                 break;
             }
             i += cnt;
@@ -889,7 +943,7 @@ __global__ void __launch_bounds__(32) k_search_paper(const Dev<W> a)
     const int share = (n_in + gridDim.x - 1) / gridDim.x;
     const int r0 = min(n_in, blockIdx.x * share), r1 = min(n_in, r0 + share);
     for (int i = r0; i < r1; ++i) {
-        const Rec<W> r = load_rec<W>(a, frontier, n_act, in, i);
+        const Rec<W> r = load_rec<W>(a, frontier, n_act, a.ctrl->n_front, a.ctrl->cur ? a.act1 : a.act0, in, i);
         const unsigned inst0 = r.inst;
         const unsigned long long left = a.cnt.budget_left[inst0];
         const bool budgeted = left != ~0ull;
@@ -1047,11 +1101,21 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split(const Dev<W> a)
     Ctrl *ctrl = a.ctrl;
     const int k = blockIdx.x;
     const int n_active = ctrl->n_active;
-    if (k < n_active) {
+    // serving: an instance whose open nodes were carried over continues its
+    // iteration in this step (no split; its counters keep running)
+    const unsigned inst_k = k < n_active ? (ctrl->cur ? a.act1 : a.act0)[k] : 0u;
+    const bool continuing = k < n_active && a.slice && a.carry[inst_k];
+    if (continuing) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            a.count[k] = 0;
+            a.carry[inst_k] = 0;
+        }
+    } else if (k < n_active) {
         SharedLut<W>::load(lut, a.lut);
-        const unsigned inst = (ctrl->cur ? a.act1 : a.act0)[k];
+        const unsigned inst = inst_k;
         const InstState<W> st = a.state[inst];
-        Rec<W> *A = a.scratch + (size_t)k * 2 * a.C;
+        Rec<W> *A = a.scratch + region_of(a, k, inst);
         Rec<W> *Bg = A + a.C;
         const B GOAL = goal_board<W>();
         if (threadIdx.x == 0) {
@@ -1178,6 +1242,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split(const Dev<W> a)
     if (threadIdx.x == 0)
         s_carry = 0;
     __syncthreads();
+    const unsigned *act = ctrl->cur ? a.act1 : a.act0;
     for (int base = 0; base < n_active; base += blockDim.x) {
         const int j = base + threadIdx.x;
         const int v = j < n_active ? __ldcg(&a.count[j]) : 0;
@@ -1185,6 +1250,11 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split(const Dev<W> a)
         const int pos = block_exclusive_scan(v, warp_sums, &total);
         if (j < n_active)
             a.offset[j] = s_carry + pos;
+        if (j < n_active && a.slice && v > 0) {
+            // the frontier numbering of this iteration, kept while it runs
+            a.fbase[act[j]] = s_carry + pos;
+            a.fcount[act[j]] = v;
+        }
         __syncthreads();
         if (threadIdx.x == 0)
             s_carry += total;
@@ -1192,11 +1262,16 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split(const Dev<W> a)
     }
     if (threadIdx.x == 0) {
         ctrl->done_blocks = 0;
-        ctrl->n_in = s_carry;
+        // the first pass reads the frontiers, then the carried open nodes
+        const int carried = a.slice ? ctrl->n_carry : 0;
+        ctrl->n_front = s_carry;
+        ctrl->n_in = s_carry + carried;
         ctrl->head = 0;
         ctrl->out_count = 0;
         ctrl->exited = 0;
-        ctrl->qi = 0;
+        ctrl->qi = carried ? ctrl->carry_q : 0;
+        ctrl->n_carry = 0;
+        ctrl->step_t0 = global_ns();
         ctrl->first_pass = 1;
         ctrl->passes_step = 0;
         ctrl->t_start = ~0ull;
@@ -1227,7 +1302,14 @@ __device__ void end_of_pass(const Dev<W> &a)
     c->max_out = max(c->max_out, c->out_count);
     if (c->passes_step >= MAX_PASSES_PER_STEP)
         c->err |= ERR_INTERNAL;
-    const bool again = c->out_count > 0 && c->err == 0;
+    bool again = c->out_count > 0 && c->err == 0;
+    if (again && slice_over(a)) {
+        // serving: the step's time slice is over; the open nodes wait in the
+        // output queue and the next step continues their iterations
+        c->n_carry = c->out_count;
+        c->carry_q = c->qi ^ 1;
+        again = false;
+    }
     c->pass_again = again ? 1 : 0;
     if (again) {
         c->n_in = c->out_count;
@@ -1250,10 +1332,12 @@ template <int W>
 __device__ bool take_goal_record(const Dev<W> &a, const CallDesc &dsc, int k, unsigned inst, InstState<W> &st)
 {
     const unsigned go = a.cnt.goal_origin[inst];
-    const int local = (int)go - a.offset[k];
-    if (go == 0xffffffffu || local < 0 || local >= a.count[k])
+    const int base = a.slice ? a.fbase[inst] : a.offset[k];
+    const int cnt = a.slice ? a.fcount[inst] : a.count[k];
+    const int local = (int)go - base;
+    if (go == 0xffffffffu || local < 0 || local >= cnt)
         return false;
-    const Rec<W> r = a.scratch[(size_t)k * 2 * a.C + local];
+    const Rec<W> r = a.scratch[region_of(a, k, inst) + local];
     const int d = (int)m_hi(r.meta);
     // every step must descend, and a goal can only sit at depth == limit
     if (st.path_len + d > st.limit || (st.mode == MODE_PATH && d == 0))
@@ -1288,6 +1372,12 @@ __global__ void k_advance(const Dev<W> a)
         const CallDesc dsc = *a.desc;
         const unsigned inst = (ctrl->cur ? a.act1 : a.act0)[k];
         unsigned *next_active = ctrl->cur ? a.act0 : a.act1;
+        if (a.slice && a.carry[inst]) {
+            // its iteration continues in the next step
+            next_active[atomicAdd(&ctrl->n_next, 1)] = inst;
+            goto advanced;
+        }
+        {
         InstState<W> st = a.state[inst];
         const unsigned long long total = a.cnt.split_nodes[inst] + a.cnt.search_nodes[inst];
         const unsigned long long goals = a.cnt.goals[inst];
@@ -1344,6 +1434,8 @@ __global__ void k_advance(const Dev<W> a)
         } else if (a.done_list) {
             a.done_list[atomicAdd(&ctrl->n_done, 1)] = inst;
         }
+        }
+    advanced:;
     }
     if (!last_block_done<W>((unsigned *)&ctrl->done_blocks, &s_last))
         return;
@@ -1492,12 +1584,27 @@ __global__ void k_admit(const Dev<W> a, const unsigned *slot, const uint64_t *bo
         return;
     const CallDesc dsc = *a.desc;
     const unsigned i = slot[j];
+    if (a.carry)
+        a.carry[i] = 0;
     if (init_instance<W>(a, dsc, (int)i, load_board<W>(boards, (size_t)j))) {
         const int k = atomicAdd(&a.ctrl->n_active, 1);
         (a.ctrl->cur ? a.act1 : a.act0)[k] = i;
     } else {
         a.done_list[atomicAdd(&a.ctrl->n_done, 1)] = i;
     }
+}
+
+// Serving: marks the instances whose open nodes were carried over at the end
+// of a step's time slice (they neither advance now nor split next step).
+template <int W>
+__global__ void k_carry_mark(const Dev<W> a)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const Ctrl *c = a.ctrl;
+    if (j >= c->n_carry)
+        return;
+    const Rec<W> *q = c->carry_q ? a.q1 : a.q0;
+    a.carry[q[j].inst] = 1u;
 }
 
 template <int W>

@@ -8,6 +8,11 @@
 // One host thread per server drives the device loop:
 //   admit (k_admit) -> one threshold step (k_split, k_search passes,
 //   k_advance) -> harvest the instances that finished (k_pack)
+// A step is time-sliced: once it has run for the slice, the search passes
+// stop and the open nodes of every unfinished iteration are carried into the
+// next step (k_carry_mark), so that requests whose iterations are short
+// advance, finish and free their slots without waiting for the longest
+// iteration of the batch, and new requests join sooner.
 // using the same kernels as bpida_solve_ex. The number of slots is bounded
 // by the frontier memory the caller grants (each slot owns 2*C frontier
 // records), so admission is by frontier memory.
@@ -105,6 +110,7 @@ struct bpida_server {
     int in_flight = 0;
     bool stop = false;
     std::atomic<bool> failed{false};
+    std::atomic<long long> slice_ns{2000000};
     bpida_server_stats stats;
     std::thread th;
 
@@ -138,7 +144,8 @@ bool bpida_server::device_step(int admitted)
     SV_CK(cudaMemcpyAsync(h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     SV_CK(cudaStreamSynchronize(st));
     const int n_active = h_ctrl->n_active;
-    uint64_t passes = 0, steps = 0;
+    uint64_t passes = 0, steps = 0, sliced = 0;
+    d.tune.step_ns = (unsigned long long)std::max(0ll, slice_ns.load());
     if (n_active > 0) {
         k_split<SV_W><<<n_active, SPLIT_THREADS, 0, st>>>(d);
         SV_CK(cudaGetLastError());
@@ -150,6 +157,11 @@ bool bpida_server::device_step(int admitted)
             ++passes;
             if (!h_ctrl->pass_again)
                 break;
+        }
+        if (h_ctrl->n_carry > 0) {
+            k_carry_mark<SV_W><<<(h_ctrl->n_carry + 255) / 256, 256, 0, st>>>(d);
+            SV_CK(cudaGetLastError());
+            ++sliced;
         }
         k_advance<SV_W><<<(n_active + 127) / 128, 128, 0, st>>>(d);
         SV_CK(cudaGetLastError());
@@ -170,6 +182,7 @@ bool bpida_server::device_step(int admitted)
         std::lock_guard<std::mutex> lock(mu);
         stats.passes += passes;
         stats.steps += steps;
+        stats.sliced_steps += sliced;
         stats.max_active = std::max(stats.max_active, n_active);
     }
     if (n_done > 0) {
@@ -311,6 +324,7 @@ bpida_server *bpida_server_create(const bpida_config *cfg, size_t frontier_bytes
     const size_t o_len = take(4 * n), o_moves = take(SV_MAXLEN * n), o_nodes = take(8 * SV_MAXIT * n),
                  o_iters = take(4 * n), o_status = take(4 * n);
     const size_t o_ovf = take((size_t)total_warps * ovf_cap * WarpStack<SV_W>::ENTRY_BYTES);
+    const size_t o_carry = take(4 * n), o_fbase = take(4 * n), o_fcount = take(4 * n);
     if (cudaMalloc(&sv->mem, off) != cudaSuccess) {
         delete sv;
         return nullptr;
@@ -332,6 +346,10 @@ bpida_server *bpida_server_create(const bpida_config *cfg, size_t frontier_bytes
     d.Q = (int)Q;
     d.ovf = (unsigned char *)(b + o_ovf);
     d.ovf_cap = ovf_cap;
+    d.slice = 1;
+    d.carry = (unsigned *)(b + o_carry);
+    d.fbase = (int *)(b + o_fbase);
+    d.fcount = (int *)(b + o_fcount);
     {
         char *p = b + o_ctr;
         d.cnt.search_nodes = (unsigned long long *)p;
@@ -377,6 +395,7 @@ bpida_server *bpida_server_create(const bpida_config *cfg, size_t frontier_bytes
     ok = ok && cudaMallocHost((void **)&sv->h_admit_board, 8 * n) == cudaSuccess;
     ok = ok && cudaMallocHost((void **)&sv->h_packed, sizeof(Packed) * n) == cudaSuccess;
     ok = ok && cudaMallocHost((void **)&sv->h_ctrl, sizeof(Ctrl)) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(d.carry, 0, 4 * n, sv->st) == cudaSuccess;
     if (ok) {
         k_set_desc<<<1, 1, 0, sv->st>>>(desc, (CallDesc *)(b + o_desc), d.ctrl);
         ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(sv->st) == cudaSuccess;
@@ -438,6 +457,12 @@ void bpida_server_get_stats(bpida_server *sv, bpida_server_stats *out)
 }
 
 double bpida_server_clock(void) { return now_s(); }
+
+void bpida_server_set_time_slice(bpida_server *sv, int microseconds)
+{
+    if (sv)
+        sv->slice_ns = microseconds > 0 ? 1000ll * microseconds : 0ll;
+}
 
 void bpida_server_destroy(bpida_server *sv)
 {

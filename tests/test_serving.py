@@ -87,3 +87,64 @@ def test_serving_rejects_bad_boards_and_keeps_going():
     assert got[1]["status"] == bpida.EINVAL and got[1]["length"] == -1
     ref = oracle.solve(4, good.tiles)
     assert got[2]["status"] == 0 and got[2]["nodes"] == ref.nodes and got[2]["moves"] == ref.moves
+
+
+def _mix_with_perms(n_walks, perm_ranks):
+    rng = I.Xoshiro256ss(777)
+    insts = [I.make_walk(4, 61000 + i, rng.uniform_int(20, 56)) for i in range(n_walks)]
+    with open(os.path.join(GOLDEN, "perms15_100.json")) as f:
+        doc = json.load(f)
+    order = sorted(doc["instances"], key=lambda r: sum(r["nodes"]))
+    perms = I.perms15_100()
+    return insts + [perms[order[k]["index"]] for k in perm_ranks]
+
+
+def test_time_sliced_steps_give_the_same_results():
+    """With a 50-microsecond time slice the permutations' iterations run over
+    many steps, their open nodes carried from step to step, while the walks
+    advance and finish: every result equals the board's solo result and the
+    oracle's."""
+    insts = _mix_with_perms(60, [0, 1, 2, 3, 40, 60])
+    solo = [_alone(x)[0] for x in insts]
+    packed = [int(w) for w in I.packed_array(insts)]
+    with bpida.Server(frontier_bytes=256 << 20, max_slots=48, time_slice_us=50) as sv:
+        for i, w in enumerate(packed):
+            sv.submit(w, i)
+            if i % 20 == 19:
+                time.sleep(0.005)
+        got = _drain(sv, len(insts))
+        stats = sv.stats()
+    for i, r in enumerate(solo):
+        g = got[i]
+        assert g["status"] == r["status"] == 0
+        assert (g["length"], g["nodes"], g["moves"], g["solutions"]) == (r["length"], r["nodes"], r["moves"],
+                                                                          r["solutions"]), i
+    ref = oracle.solve_batch(4, I.tiles_array(insts))
+    for i, o in enumerate(ref):
+        assert got[i]["nodes"] == o.nodes and got[i]["moves"] == o.moves
+    assert stats["sliced_steps"] > 0
+
+
+def _easy_latencies(slice_us):
+    insts = _mix_with_perms(40, [99])
+    packed = [int(w) for w in I.packed_array(insts)]
+    with bpida.Server(frontier_bytes=256 << 20, max_slots=64, time_slice_us=slice_us) as sv:
+        sv.submit(packed[-1], len(insts) - 1)  # the hardest board first (~1e10 nodes)
+        time.sleep(0.02)                      # it is into its long iterations by now
+        for i in range(len(insts) - 1):
+            sv.submit(packed[i], i)
+        got = _drain(sv, len(insts))
+    lat = sorted(got[i]["latency_s"] for i in range(len(insts) - 1))
+    return lat[len(lat) // 2], got
+
+
+def test_time_slices_let_short_requests_pass_a_long_one():
+    """Forty easy walks submitted while the hardest permutation is in its long
+    iterations: with a 500-microsecond slice they are admitted and finish
+    while the permutation still searches; without slices every step waits
+    for the permutation's iteration."""
+    sliced, got_s = _easy_latencies(500)
+    whole, got_w = _easy_latencies(0)
+    for i in got_s:
+        assert got_s[i]["nodes"] == got_w[i]["nodes"] and got_s[i]["moves"] == got_w[i]["moves"]
+    assert sliced < 0.5 * whole, (sliced, whole)
