@@ -43,8 +43,9 @@ struct DevBuf {
     size_t n = 0;
 };
 
-// W, S, warps per block, n, frontier cap, hand-back percentage, min rounds, min pass time, variant
-typedef std::tuple<int, int, int, int, int, int, int, int, int> PlanKey;
+// W, S, warps per block, n, frontier cap, hand-back percentage, min rounds, min pass time, variant,
+// fused iterations
+typedef std::tuple<int, int, int, int, int, int, int, int, int, int> PlanKey;
 
 struct Plan {
     cudaGraph_t graph = nullptr;
@@ -63,7 +64,7 @@ struct Plan {
 };
 
 struct Workspace {
-    DevBuf state, act0, act1, ctr, scratch, count, offset, q0, q1, ctrl, desc, ovf;
+    DevBuf state, act0, act1, ctr, scratch, count, offset, q0, q1, ctrl, desc, ovf, fuse;
     Ctrl *h_ctrl = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     unsigned gen = 1;  // bumped whenever a buffer moves
@@ -113,7 +114,8 @@ struct Workspace {
         for (auto &kv : plans)
             kv.second.destroy();
         plans.clear();
-        DevBuf *all[] = {&state, &act0, &act1, &ctr, &scratch, &count, &offset, &q0, &q1, &ctrl, &desc, &ovf};
+        DevBuf *all[] = {&state, &act0, &act1, &ctr, &scratch, &count, &offset, &q0, &q1, &ctrl, &desc, &ovf,
+                         &fuse};
         for (DevBuf *b : all) {
             if (b->p)
                 cudaFree(b->p);
@@ -147,6 +149,15 @@ struct Settings {
     int width, count_all, split_target, wpb, S, exit_pct, min_rounds, driver, min_pass_ns, variant;
     uint64_t budget;
 };
+
+// A step fuses the next iterations of an instance while the highest of them
+// is predicted (x tune.growth per iteration) to expand at most this many
+// nodes (divided among the step's instances): the small early iterations
+// share one step instead of one each. Calls with at most FUSE_MAX_N boards
+// use it (their steps are few and short, so the steps saved pay); larger
+// batches run the kernel without the fused counts.
+constexpr unsigned long long FUSE_NODES = 8000000ull;
+constexpr int FUSE_MAX_N = 8;
 
 #define CK(x)                                                                                     \
     do {                                                                                          \
@@ -191,11 +202,12 @@ struct Geometry {
     size_t smem, Q;
     int n_cap;
     int variant;
+    bool fuse;
 };
 
-template <int W, int S> void (*search_kernel(int variant))(const Dev<W>)
+template <int W, int S> void (*search_kernel(int variant, bool fuse))(const Dev<W>)
 {
-    return variant == 1 ? k_search_paper<W, S> : k_search<W, S>;
+    return variant == 1 ? k_search_paper<W, S> : fuse ? k_search<W, S, true> : k_search<W, S, false>;
 }
 
 // The whole solve as one graph (k_set_desc is launched before it):
@@ -244,7 +256,7 @@ cudaError_t build_graph(Plan &pl, Dev<W> d, const Geometry &g, const char **wher
 
     cudaGraphNode_t n_search;
     *where = "search node";
-    if ((e = add_kernel(&n_search, P, nullptr, 0, search_kernel<W, S>(g.variant), dim3(g.grid), dim3(g.threads),
+    if ((e = add_kernel(&n_search, P, nullptr, 0, search_kernel<W, S>(g.variant, g.fuse), dim3(g.grid), dim3(g.threads),
                         g.smem, d)) != cudaSuccess)
         return e;
     *where = "cudaGraphInstantiate";
@@ -264,29 +276,33 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     Geometry g;
     g.n_cap = n;
     g.variant = cfg.variant;
+    // fused iterations: all-solutions mode of this kernel, no node budget,
+    // a call of at most FUSE_MAX_N boards
+    const bool fuse = cfg.variant == 0 && cfg.count_all == 1 && cfg.budget == 0 && n <= FUSE_MAX_N;
+    g.fuse = fuse;
     const int wpb = cfg.variant == 1 ? 1 : cfg.wpb;  // the paper's kernel: block = warp
     g.threads = wpb * 32;
     g.smem = SharedLut<W>::BYTES + (size_t)wpb * S * WarpStack<W>::ENTRY_BYTES;
     // one kernel serves every block size (and the serving path), so its
     // dynamic shared memory limit is set once to the device's maximum; the
-    // blocks per SM are looked up once per (device, block size, variant)
-    static std::map<std::pair<int, int>, int> smem_limit;
-    int &lim = smem_limit[std::make_pair(dev, cfg.variant)];
+    // blocks per SM are looked up once per (device, block size, kernel)
+    static std::map<std::tuple<int, int, int>, int> smem_limit;
+    int &lim = smem_limit[std::make_tuple(dev, cfg.variant, fuse ? 1 : 0)];
     if (lim == 0) {
         // the device maximum less the kernel's static shared memory
         int optin = 0;
         cudaFuncAttributes fa;
         CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        CK(cudaFuncGetAttributes(&fa, search_kernel<W, S>(cfg.variant)));
+        CK(cudaFuncGetAttributes(&fa, search_kernel<W, S>(cfg.variant, fuse)));
         lim = optin - (int)fa.sharedSizeBytes;
-        CK(cudaFuncSetAttribute(search_kernel<W, S>(cfg.variant), cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        CK(cudaFuncSetAttribute(search_kernel<W, S>(cfg.variant, fuse), cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     }
     if (g.smem > (size_t)lim)
         return BPIDA_EINVAL;
-    static std::map<std::tuple<int, int, int>, int> occ;
-    int &bpsm = occ[std::make_tuple(dev, wpb, cfg.variant)];
+    static std::map<std::tuple<int, int, int, int>, int> occ;
+    int &bpsm = occ[std::make_tuple(dev, wpb, cfg.variant, fuse ? 1 : 0)];
     if (bpsm == 0)
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, search_kernel<W, S>(cfg.variant), g.threads, g.smem));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, search_kernel<W, S>(cfg.variant, fuse), g.threads, g.smem));
     if (bpsm < 1)
         return BPIDA_EINVAL;
     g.grid = sms * bpsm;
@@ -313,6 +329,8 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     CK(ws.ensure(ws.ctrl, sizeof(Ctrl)));
     CK(ws.ensure(ws.desc, sizeof(CallDesc)));
     CK(ws.ensure(ws.ovf, (size_t)g.total_warps * ovf_cap * WarpStack<W>::ENTRY_BYTES));
+    if (fuse)
+        CK(ws.ensure(ws.fuse, (size_t)n * (sizeof(int) + FUSE_K * (2 * sizeof(unsigned long long) + sizeof(unsigned)))));
     if (!ws.h_ctrl)
         CK(cudaMallocHost((void **)&ws.h_ctrl, sizeof(Ctrl)));
     if (!ws.ev0) {
@@ -336,6 +354,17 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     d.Q = (int)g.Q;
     d.ovf = (unsigned char *)ws.ovf.p;
     d.ovf_cap = ovf_cap;
+    if (fuse) {
+        char *p = (char *)ws.fuse.p;
+        d.fuse.low = (unsigned long long *)p;
+        p += sizeof(unsigned long long) * FUSE_K * n;
+        d.fuse.goals = (unsigned long long *)p;
+        p += sizeof(unsigned long long) * FUSE_K * n;
+        d.fuse.origin = (unsigned *)p;
+        p += sizeof(unsigned) * FUSE_K * n;
+        d.fuse.jump = (int *)p;
+        d.fuse.max_nodes = FUSE_NODES;
+    }
     {
         char *p = (char *)ws.ctr.p;
         d.cnt.search_nodes = (unsigned long long *)p;
@@ -385,7 +414,8 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     const dim3 b128(128), bsplit(SPLIT_THREADS);
     const dim3 g_inst((n + 127) / 128);
     if (cfg.driver == 0) {
-        const PlanKey key(W, S, cfg.wpb, n, g.tcap, cfg.exit_pct, cfg.min_rounds, cfg.min_pass_ns, cfg.variant);
+        const PlanKey key(W, S, cfg.wpb, n, g.tcap, cfg.exit_pct, cfg.min_rounds, cfg.min_pass_ns, cfg.variant,
+                          fuse ? 1 : 0);
         auto found = ws.plans.find(key);
         if (found == ws.plans.end() || !found->second.exec || found->second.gen != ws.gen) {
             ws.trim_plans();
@@ -423,7 +453,7 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
             for (;;) {
                 if (g_timing)
                     CK(cudaEventRecord(ws.ev0, st));
-                search_kernel<W, S>(cfg.variant)<<<g.grid, g.threads, g.smem, st>>>(d);
+                search_kernel<W, S>(cfg.variant, fuse)<<<g.grid, g.threads, g.smem, st>>>(d);
                 CK(cudaGetLastError());
                 if (g_timing)
                     CK(cudaEventRecord(ws.ev1, st));

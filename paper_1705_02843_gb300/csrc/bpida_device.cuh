@@ -245,7 +245,7 @@ template <int W> struct InstState {
     int status;
     int length;
     uint32_t target;             // frontier records wanted from the next split
-    uint32_t pad;
+    int jump;                    // iterations fused above `limit` in the current step (see Fuse)
     unsigned long long cum_nodes;
     unsigned long long solutions;
 };
@@ -261,6 +261,29 @@ struct Counters {
                                        // bit 1: first-solution mode found a goal
 };
 static constexpr unsigned ABORT_BUDGET = 1u, ABORT_FOUND = 2u;
+
+// Fused iterations. The Manhattan distance is consistent (h changes by
+// exactly 1 per move), so f never decreases along a path, and sequential
+// IDA* at limit L pops exactly the nodes with f <= L whose ancestors are not
+// goals. One search at limit L + 2J therefore pops the nodes of the
+// iterations L, L + 2, ..., L + 2J together; counting the popped nodes by
+// slack (limit + 2J - f) gives each of those iterations' node count, and
+// counting goals by slack gives the first limit with a solution, its number
+// of optimal solutions and its first goal-bearing frontier record. A step
+// fuses the iterations whose counts are predicted to stay small, so the
+// results are exactly those of one iteration per step.
+static constexpr int FUSE_MAX = 6;  // at most FUSE_MAX + 1 iterations per step
+static constexpr int FUSE_K = 8;    // per-instance entries of the fused counters
+struct Fuse {
+    int *jump;                     // per instance: J of this step (null: no fusion)
+    unsigned long long *low;       // per instance x FUSE_K: nodes popped (split and search) with slack 2m, m < J
+    unsigned long long *goals;     // per instance x FUSE_K: goals popped with slack 2(J - j), by j
+    unsigned *origin;              // per instance x FUSE_K: smallest origin of such a goal, by j
+    unsigned long long max_nodes;  // fuse while the top iteration is predicted below this,
+                                   // divided among the instances of the step (nodes that
+                                   // overshoot the optimum cost every instance; the
+                                   // steps saved are shared)
+};
 
 struct Tune {
     int min_rounds;      // rounds before a warp may hand its stack back
@@ -347,6 +370,7 @@ template <int W> struct Dev {
     unsigned *done_list;        // serving: instances that finished in this step (else null)
     unsigned char *ovf;         // per-warp overflow stacks in global memory (may be null)
     int ovf_cap;                // entries per warp overflow stack (0 = none)
+    Fuse fuse;                  // fused iterations (fuse.jump null: one iteration per step)
     // Serving with time slices (slice = 1): an instance's iteration may run
     // over several steps. Frontier regions then belong to instance slots, not
     // to positions in the active list; carry[i] = 1 marks a slot whose open
@@ -607,7 +631,9 @@ template <int W> __device__ void end_of_pass(const Dev<W> &a);
 // the others only contribute f_next. The warp takes runs of same-instance
 // records from the pass's input queue until it is exhausted; once enough
 // warps have run dry, busy warps hand their open nodes to the next pass.
-template <int W, int S>
+// FUSE: the kernel also counts popped nodes and goals by slack for fused
+// iterations (see Fuse); without it that code is compiled out.
+template <int W, int S, bool FUSE = false>
 __global__ void k_search(const Dev<W> a)
 {
     typedef typename Geo<W>::B B;
@@ -617,6 +643,7 @@ __global__ void k_search(const Dev<W> a)
     // counters see one atomic per block instead of one per warp
     __shared__ int s_warps_done;
     __shared__ unsigned long long s_t_end, s_nodes;
+    __shared__ unsigned s_low[FUSE ? 32 : 1][FUSE_MAX];  // fused iterations: per warp, pops with slack 2m
     unsigned char *lut = smem;
     if (threadIdx.x == 0) {
         atomicMin(&a.ctrl->t_start, global_ns());
@@ -659,6 +686,13 @@ __global__ void k_search(const Dev<W> a)
     unsigned acc_inst = 0xffffffffu;
     unsigned long long acc_nodes = 0, tot_nodes = 0;
     int fmin = INT_MAX;
+    // fused iterations: nodes popped with slack 2m (m < acc_J) of acc_inst,
+    // counted by lane 0 in shared memory
+    int acc_J = 0;
+    unsigned *lowc = s_low[FUSE ? warp : 0];
+    if (FUSE && lane == 0)
+        for (int m = 0; m < FUSE_MAX; ++m)
+            lowc[m] = 0;
     auto publish = [&]() {
         const int fm = warp_min_int(fmin);
         if (lane == 0 && acc_inst != 0xffffffffu) {
@@ -666,6 +700,11 @@ __global__ void k_search(const Dev<W> a)
                 atomicAdd(&a.cnt.search_nodes[acc_inst], acc_nodes);
             if (fm != INT_MAX)
                 atomicMin(&a.cnt.fnext_off[acc_inst], fm);
+            for (int m = 0; FUSE && m < acc_J; ++m)
+                if (lowc[m]) {
+                    atomicAdd(&a.fuse.low[(size_t)acc_inst * FUSE_K + m], (unsigned long long)lowc[m]);
+                    lowc[m] = 0;
+                }
         }
         acc_nodes = 0;
         fmin = INT_MAX;
@@ -703,7 +742,9 @@ __global__ void k_search(const Dev<W> a)
             if (inst0 != acc_inst) {
                 publish();
                 acc_inst = inst0;
+                acc_J = (FUSE && a.fuse.jump) ? a.fuse.jump[inst0] : 0;
             }
+            const int J = FUSE ? acc_J : 0;
             __syncwarp();
             unsigned long long nodes = 0, flushed = 0;
 
@@ -776,9 +817,25 @@ __global__ void k_search(const Dev<W> a)
                         if (first_only)
                             atomicOr(&a.cnt.aborted[inst0], ABORT_FOUND);
                     }
+                    if (FUSE && J && goal) {
+                        // a goal at slack s belongs to iteration J - s/2 of the step
+                        const int j = J - (int)((mt >> 12) & 127u);
+                        if (j >= 0) {
+                            atomicAdd(&a.fuse.goals[(size_t)inst0 * FUSE_K + j], 1ull);
+                            atomicMin(&a.fuse.origin[(size_t)inst0 * FUSE_K + j], org);
+                        }
+                    }
                 }
                 const uint32_t sh_p = mt & 127u;
                 const int s = (int)((mt >> 11) & 255u);
+                if (FUSE && J) {
+                    // popped nodes above the lower limits of the step
+                    for (int m = 0; m < J; ++m) {
+                        const unsigned c = __popc(__ballot_sync(FULL, act && s == 2 * m));
+                        if (lane == 0)
+                            lowc[m] += c;
+                    }
+                }
                 const unsigned allowed = (act && !goal) ? (LegalMoves<W>::at_sh(sh_p) & ~((mt >> 7) & 15u)) : 0u;
                 const bool low = s < 2;
                 const uint32_t sbase = mt & (255u << 11);
@@ -1097,6 +1154,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split(const Dev<W> a)
     __shared__ int warp_sums[32];
     __shared__ int s_fmin, s_last, s_carry;
     __shared__ unsigned long long s_internal;
+    __shared__ unsigned s_low[FUSE_MAX];  // expanded nodes with slack 2m, m < J (fused steps)
 
     Ctrl *ctrl = a.ctrl;
     const int k = blockIdx.x;
@@ -1134,8 +1192,16 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split(const Dev<W> a)
             a.cnt.goals[inst] = 0;
             a.cnt.goal_origin[inst] = 0xffffffffu;
             a.cnt.aborted[inst] = 0;
+            for (int m = 0; m < FUSE_MAX; ++m)
+                s_low[m] = 0;
+            if (a.fuse.jump)
+                for (int j = 0; j < FUSE_K; ++j) {
+                    a.fuse.goals[(size_t)inst * FUSE_K + j] = 0;
+                    a.fuse.origin[(size_t)inst * FUSE_K + j] = 0xffffffffu;
+                }
         }
         __syncthreads();
+        const int J = a.fuse.jump ? st.jump : 0;
 
         const int T = max(1, (int)st.target);
         int cnt = 1, depth = 0;
@@ -1172,6 +1238,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split(const Dev<W> a)
                     const int p = (int)m_blank(r.meta);
                     const int last = (int)m_last(r.meta);
                     const int s = m_slack(r.meta);
+                    if (s < 2 * J)
+                        atomicAdd(&s_low[s >> 1], 1u);
                     const uint32_t d = m_hi(r.meta);
                     const LutRow<W> e = SharedLut<W>::row(lut, p);
 #pragma unroll
@@ -1228,6 +1296,9 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split(const Dev<W> a)
             a.count[k] = cnt;
             a.cnt.split_nodes[inst] = s_internal;
             a.cnt.fnext_off[inst] = s_fmin;
+            if (a.fuse.jump)
+                for (int m = 0; m < FUSE_K; ++m)
+                    a.fuse.low[(size_t)inst * FUSE_K + m] = m < J ? s_low[m] : 0ull;
             // nodes the search may still pop in this iteration within the
             // budget (counted iterations only; path recovery is not budgeted)
             const unsigned long long budget = a.desc->node_budget;
@@ -1328,10 +1399,13 @@ __device__ void end_of_pass(const Dev<W> &a)
 // Advance: per problem, close the iteration (Algorithm 1's driver). The
 // last block closes the step: the problems still active form the next one.
 // ---------------------------------------------------------------------
+// go: the smallest origin of a goal-bearing record; shift: how far the
+// search limit of the step was above st.limit (fused iterations), which the
+// record's slack is reduced by.
 template <int W>
-__device__ bool take_goal_record(const Dev<W> &a, const CallDesc &dsc, int k, unsigned inst, InstState<W> &st)
+__device__ bool take_goal_record(const Dev<W> &a, const CallDesc &dsc, int k, unsigned inst, InstState<W> &st,
+                                 unsigned go, int shift)
 {
-    const unsigned go = a.cnt.goal_origin[inst];
     const int base = a.slice ? a.fbase[inst] : a.offset[k];
     const int cnt = a.slice ? a.fcount[inst] : a.count[k];
     const int local = (int)go - base;
@@ -1353,9 +1427,12 @@ __device__ bool take_goal_record(const Dev<W> &a, const CallDesc &dsc, int k, un
         st.mode = MODE_DONE;
         st.status = 0;
     } else {
+        const int slack = m_slack(r.meta) - shift;
+        if (slack < 0)
+            return false;
         st.mode = MODE_PATH;
         st.root = r.b;
-        st.root_meta = r.meta & M_NODE_MASK;
+        st.root_meta = m_make(m_blank(r.meta), m_last(r.meta), (uint32_t)slack);
         st.target = (uint32_t)max(2, a.tune.target_path);
     }
     return true;
@@ -1388,18 +1465,56 @@ __global__ void k_advance(const Dev<W> a)
             st.mode = MODE_DONE;
             st.status = 4;  // BPIDA_EBUDGET
         } else if (st.mode == MODE_COUNT) {
-            dsc.out_nodes[(size_t)inst * Geo<W>::MAXIT + st.it] = total;
-            st.rows = st.it + 1;
-            st.cum_nodes += total;
-            if (goals > 0) {
+            // the step's iterations: limits st.limit + 2j, j = 0..J (J = 0:
+            // one iteration); the first with a goal ends the count
+            const int J = a.fuse.jump ? st.jump : 0;
+            const size_t fk = (size_t)inst * FUSE_K;
+            int jg = -1;
+            unsigned long long gj = goals;
+            if (J == 0) {
+                if (goals > 0)
+                    jg = 0;
+            } else {
+                for (int j = 0; j <= J; ++j) {
+                    const unsigned long long g = a.fuse.goals[fk + j];
+                    if (g) {
+                        jg = j;
+                        gj = g;
+                        break;
+                    }
+                }
+            }
+            const int last = jg >= 0 ? jg : J;
+            // iteration j leaves out the popped nodes whose slack is below 2(J - j)
+            unsigned long long excl = 0;
+            for (int m = 0; m < J; ++m)
+                excl += a.fuse.low[fk + m];
+            unsigned long long cnt_last = 0;
+            for (int j = 0; j <= last; ++j) {
+                cnt_last = total - excl;
+                dsc.out_nodes[(size_t)inst * Geo<W>::MAXIT + st.it + j] = cnt_last;
+                st.cum_nodes += cnt_last;
+                if (J - j - 1 >= 0)
+                    excl -= a.fuse.low[fk + J - j - 1];
+            }
+            st.rows = st.it + last + 1;
+            if (jg >= 0) {
+                st.it += jg;
+                st.limit += 2 * jg;
                 st.length = st.limit;
-                st.solutions = goals;
-                if (!take_goal_record<W>(a, dsc, k, inst, st)) {
+                st.solutions = gj;
+                const unsigned go = J ? a.fuse.origin[fk + jg] : a.cnt.goal_origin[inst];
+                st.jump = 0;
+                if (a.fuse.jump)
+                    a.fuse.jump[inst] = 0;
+                if (!take_goal_record<W>(a, dsc, k, inst, st, go, 2 * (J - jg))) {
                     st.mode = MODE_DONE;
                     st.status = 8;  // BPIDA_EINTERNAL
                     atomicOr(&ctrl->err, ERR_INTERNAL);
                 }
             } else {
+                st.it += J;
+                st.limit += 2 * J;
                 const int off = a.cnt.fnext_off[inst];
                 if (off == INT_MAX || off <= 0) {
                     st.mode = MODE_DONE;
@@ -1412,16 +1527,30 @@ __global__ void k_advance(const Dev<W> a)
                     st.limit += off;
                     st.it += 1;
                     st.root = st.start;
-                    st.root_meta = m_make(m_blank(st.start_meta), LAST_NONE, (uint32_t)(st.limit - st.h0));
-                    unsigned long long want =
-                        (total * (unsigned long long)a.tune.growth) / (unsigned long long)a.tune.nodes_per_record;
+                    const unsigned long long g = (unsigned long long)a.tune.growth;
+                    // fuse the next iterations while the top one is predicted small
+                    int Jn = 0;
+                    unsigned long long pred = cnt_last * g;
+                    const unsigned long long cap = a.fuse.max_nodes / (unsigned long long)max(1, n_active);
+                    if (a.fuse.jump)
+                        while (Jn < FUSE_MAX && pred * g <= cap && st.it + Jn + 1 < Geo<W>::MAXIT &&
+                               st.limit + 2 * (Jn + 1) <= Geo<W>::MAXLEN) {
+                            pred *= g;
+                            ++Jn;
+                        }
+                    st.jump = Jn;
+                    if (a.fuse.jump)
+                        a.fuse.jump[inst] = Jn;
+                    st.root_meta =
+                        m_make(m_blank(st.start_meta), LAST_NONE, (uint32_t)(st.limit + 2 * Jn - st.h0));
+                    unsigned long long want = pred / (unsigned long long)a.tune.nodes_per_record;
                     want = want < 1ull ? 1ull : want;
                     want = want > (unsigned long long)a.tune.target_cap ? (unsigned long long)a.tune.target_cap : want;
                     st.target = (uint32_t)want;
                 }
             }
         } else if (st.mode == MODE_PATH) {
-            if (goals == 0 || !take_goal_record<W>(a, dsc, k, inst, st)) {
+            if (goals == 0 || !take_goal_record<W>(a, dsc, k, inst, st, a.cnt.goal_origin[inst], 0)) {
                 st.mode = MODE_DONE;
                 st.status = 8;
                 atomicOr(&ctrl->err, ERR_INTERNAL);
@@ -1490,7 +1619,7 @@ __device__ bool init_instance(const Dev<W> &a, const CallDesc &dsc, int i, typen
     st.cum_nodes = 0;
     st.solutions = 0;
     st.target = 1;
-    st.pad = 0;
+    st.jump = 0;
     // permutation check, blank, Manhattan distance, parity class
     uint32_t seen = 0;
     int blank = -1, h = 0, inv = 0;
@@ -1536,7 +1665,26 @@ __device__ bool init_instance(const Dev<W> &a, const CallDesc &dsc, int i, typen
         st.root_meta = st.start_meta;
         st.mode = MODE_COUNT;
         st.status = 0;
+        if (a.fuse.jump) {
+            // the first iterations are tiny: fuse as many as the budget allows
+            const unsigned long long g = (unsigned long long)a.tune.growth;
+            const unsigned long long cap = a.fuse.max_nodes / (unsigned long long)max(1, dsc.n);
+            unsigned long long pred = g;
+            int J = 0;
+            while (J < FUSE_MAX && pred * g <= cap && J + 1 < Geo<W>::MAXIT && h + 2 * (J + 1) <= Geo<W>::MAXLEN) {
+                pred *= g;
+                ++J;
+            }
+            st.jump = J;
+            st.root_meta = m_make((uint32_t)blank, LAST_NONE, (uint32_t)(2 * J));
+            unsigned long long want = pred / (unsigned long long)a.tune.nodes_per_record;
+            want = want < 1ull ? 1ull : want;
+            want = want > (unsigned long long)a.tune.target_cap ? (unsigned long long)a.tune.target_cap : want;
+            st.target = (uint32_t)want;
+        }
     }
+    if (a.fuse.jump)
+        a.fuse.jump[i] = st.jump;
     a.state[i] = st;
     return st.mode == MODE_COUNT;
 }

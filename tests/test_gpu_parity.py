@@ -321,3 +321,36 @@ def test_paper_kernel_matches_on_permutations():
     for r, g in zip(cheap, got):
         assert g["length"] == r["length"] and g["nodes"] == r["nodes"]
         assert "".join(map(str, g["moves"])) == r["moves"]
+
+
+def test_fused_iterations_match_one_iteration_per_step():
+    """Calls of at most 8 boards fuse their small early iterations into one
+    step (one search at the highest limit, node counts split by slack); a
+    16-board call runs one iteration per step. Every result must be the same
+    and the oracle's, and the fused calls must take fewer steps than
+    iterations."""
+    insts = I.walks15_16x40()
+    tiles = [x.tiles for x in insts]
+    ref = oracle.solve_batch(4, np.array(tiles, dtype=np.uint8))
+    rc, whole = gpu_solve(4, tiles)
+    assert rc == bpida.OK
+    check_against(4, tiles, whole, ref)
+    steps_fused, iters = 0, 0
+    for i in range(16):
+        rc, one = gpu_solve(4, [tiles[i]])
+        assert rc == bpida.OK
+        steps_fused += bpida.last_stats()["steps"]
+        iters += one[0]["iters"]
+        check_against(4, [tiles[i]], one, [ref[i]])
+    assert steps_fused < iters
+    for lo in (0, 8):
+        rc, eight = gpu_solve(4, tiles[lo:lo + 8])
+        assert rc == bpida.OK
+        check_against(4, tiles[lo:lo + 8], eight, ref[lo:lo + 8])
+    # 8-puzzle states up to the diameter, one per call
+    dist, count, order = P.bfs8()
+    for s in [order[-1], order[-2], order[1000], order[50000]]:
+        rc, one = gpu_solve(3, [list(s)])
+        r = oracle.solve(3, list(s))
+        assert one[0]["length"] == dist[s] and one[0]["nodes"] == r.nodes and one[0]["solutions"] == count[s]
+        assert one[0]["moves"] == r.moves
