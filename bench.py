@@ -49,17 +49,18 @@ UNIT = "expansions/s"
 WORKLOAD_DESC = ("perms15_100: 100 seeded uniformly random solvable 15-puzzle boards "
                  "(seeds 1001-1100), Manhattan distance, all-optimal-solutions mode")
 
-# Warp instructions issued per node expanded by k_search<4,512> in steady
-# state (the work the method needs per expansion), from ncu
+# The plain form (one board per call) runs the search kernel's fused-iteration
+# variant k_search<4,512,1>. Warp instructions it issues per node expanded in
+# steady state (the work the method needs per expansion), from ncu
 # (smsp__inst_executed.sum / nodes) on the final iteration of board 0 run as
 # one pass: profiles/k_search_15puzzle_perms15_board0_final_iteration.txt.
-INSTR_PER_EXPANSION = 5.53
+INSTR_PER_EXPANSION = 5.86
 # The same ratio over every k_search launch of a plain solve of board 0
 # (hand-back on, as in the benchmark): ramp-up, short passes and hand-back
 # copies included. profiles/k_search_15puzzle_plain_solve_all_launches.txt.
-INSTR_PER_EXPANSION_PLAIN_MIX = 7.27
+INSTR_PER_EXPANSION_PLAIN_MIX = 7.65
 # DRAM bytes (read + write) per k_search launch over those launches.
-TRAFFIC_PER_LAUNCH = 1233726
+TRAFFIC_PER_LAUNCH = 1745542
 
 
 def golden_path(name):
@@ -706,7 +707,7 @@ def main():
         achieved = s_nodes * INSTR_PER_EXPANSION / (s_ms / 1e3) / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
                 "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH,
-                "kernel": "k_search<4,512>", "instr_per_expansion": INSTR_PER_EXPANSION,
+                "kernel": "k_search<4,512,1>", "instr_per_expansion": INSTR_PER_EXPANSION,
                 "launch_ms_mean": s_ms / max(s_launch, 1), "launches_timed": s_launch,
                 "issue_utilization_plain_mix": s_nodes * INSTR_PER_EXPANSION_PLAIN_MIX / (s_ms / 1e3) / 1e9 / peak,
                 "expansions_per_s_in_kernel": s_nodes / (s_ms / 1e3),
@@ -714,7 +715,7 @@ def main():
                 "peak_basis": "%d SMs x 4 schedulers x %.0f MHz median SM clock sampled during the run" % (sms, f_mhz)}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": peak, "unit": "Gwarp-inst/s", "frac": None,
-                "traffic": None, "kernel": "k_search<4,512>",
+                "traffic": None, "kernel": "k_search<4,512,1>",
                 "launch_ms_mean": s_ms / max(s_launch, 1), "launches_timed": s_launch,
                 "expansions_per_s_in_kernel": s_nodes / (s_ms / 1e3) if s_ms else None,
                 "expansions_per_s_in_kernel_timed_steps": dev_nodes / (dev_ms / 1e3) if dev_ms else None}
