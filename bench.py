@@ -488,6 +488,8 @@ def main():
                          "k_search launch is number iters-1), print its statistics and exit")
     ap.add_argument("--profile-default", action="store_true",
                     help="with --profile-case: keep the default hand-back (as in the bench)")
+    ap.add_argument("--profile-width", type=int, default=4, choices=[4, 5],
+                    help="with --profile-case: 5 = a board of the 24-puzzle walk workload")
     ap.add_argument("--profile-variant", type=int, default=0, metavar="V",
                     help="with --profile-case: solve with bpida_config.variant V (2-4: the thread-parallel "
                          "configurations; the final iteration's k_search_tp launch is number iters-1)")
@@ -526,17 +528,21 @@ def main():
 
     insts = I.WORKLOADS[args.workload]()
     if args.profile_case is not None:
-        x = insts[args.profile_case]
+        W = args.profile_width
+        # the 24-puzzle case: a walk of the 1024-walk workload, with the
+        # oracle's node budget as in that workload
+        x = (I.walks24_1024() if W == 5 else insts)[args.profile_case]
         b = torch.from_numpy(I.packed_array([x]).view(np.int64)).to(dev)
+        budget = 50_000_000 if W == 5 else 0
         for rep in range(2):
             # host-driven loop: ncu cannot see kernels inside graphs that
             # hold conditional nodes
             if args.profile_variant >= 2:
-                cfg = bpida.make_config(4, variant=args.profile_variant)
+                cfg = bpida.make_config(W, variant=args.profile_variant)
             else:
-                cfg = bpida.make_config(4, exit_fraction_pct=0 if args.profile_default else 100, driver=1,
-                                        variant=args.profile_variant)
-            s = bpida.solve(b, 4, cfg)
+                cfg = bpida.make_config(W, exit_fraction_pct=0 if args.profile_default else 100, driver=1,
+                                        variant=args.profile_variant, node_budget=budget)
+            s = bpida.solve(b, W, cfg)
             torch.cuda.synchronize(dev)
         h = s.to_host()[0]
         st = bpida.last_stats()

@@ -117,7 +117,11 @@ typedef struct {
 } bpida_config;
 
 typedef struct {
-    int steps;              /* threshold steps issued (all instances) */
+    int steps;              /* device steps issued (all instances); a call of
+                               at most 8 boards in all-solutions mode without
+                               a node budget may search several consecutive
+                               thresholds of an instance in one step, with the
+                               same per-iteration results */
     int passes;             /* search kernel launches */
     uint64_t records;       /* frontier records produced by the splitter */
     uint64_t handed_back;   /* stack entries handed back between passes */

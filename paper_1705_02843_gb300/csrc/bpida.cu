@@ -3,13 +3,14 @@
 //
 // One solve call runs all of its instances together. Every step closes one
 // f-limited iteration of every still-active instance (each at its own
-// limit): k_split builds each instance's root set (its last block computes
-// the frontier offsets), k_search passes consume the frontiers with
-// persistent warps (another pass only when warps handed work back; the last
-// warp of a pass decides), and k_advance records the iteration's node count
-// and raises each limit to the smallest pruned f, or, once a goal was
-// popped, walks down the first goal-bearing root to recover the solution
-// path (its last block closes the step).
+// limit), or several consecutive ones searched together (fused iterations,
+// calls of a few boards): k_split builds each instance's root set (its last
+// block computes the frontier offsets), k_search passes consume the
+// frontiers with persistent warps (another pass only when warps handed work
+// back; the last block of a pass decides), and k_advance records the
+// iterations' node counts and raises each limit to the smallest pruned f,
+// or, once a goal was popped, walks down the first goal-bearing root to
+// recover the solution path (its last block closes the step).
 //
 // By default the whole loop is one CUDA graph: the step loop and the pass
 // loop are conditional WHILE nodes whose conditions are set on the device,

@@ -354,3 +354,23 @@ def test_fused_iterations_match_one_iteration_per_step():
         r = oracle.solve(3, list(s))
         assert one[0]["length"] == dist[s] and one[0]["nodes"] == r.nodes and one[0]["solutions"] == count[s]
         assert one[0]["moves"] == r.moves
+
+
+def test_fused_iterations_24puzzle():
+    """The 24-puzzle's fused-iteration kernel (calls of at most 8 boards):
+    one board per call and four per call, against the oracle."""
+    insts = [I.make_walk(5, 900 + s, 30 + 2 * s) for s in range(12)]
+    tiles = [x.tiles for x in insts]
+    ref = oracle.solve_batch(5, np.array(tiles, dtype=np.uint8))
+    steps, iters = 0, 0
+    for i in range(12):
+        rc, one = gpu_solve(5, [tiles[i]])
+        assert rc == bpida.OK
+        steps += bpida.last_stats()["steps"]
+        iters += one[0]["iters"]
+        check_against(5, [tiles[i]], one, [ref[i]])
+    assert steps < iters
+    for lo in (0, 4, 8):
+        rc, four = gpu_solve(5, tiles[lo:lo + 4])
+        assert rc == bpida.OK
+        check_against(5, tiles[lo:lo + 4], four, ref[lo:lo + 4])
