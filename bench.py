@@ -561,7 +561,7 @@ def main():
     def plain_step(cfg=None):
         cfg = cfg if cfg is not None else base_cfg
         sols, agg = [], {"search_ms": 0.0, "search_ms_device": 0.0, "search_nodes": 0, "passes": 0,
-                         "launches": 0}
+                         "launches": 0, "records": 0, "handed_back": 0}
         for i in range(n):
             s = bpida.solve(boards[i:i + 1], 4, cfg)
             if s.status != bpida.OK:
@@ -577,7 +577,8 @@ def main():
         if s.status != bpida.OK:
             raise RuntimeError("solve failed: " + bpida.status_str(s.status))
         st = bpida.last_stats()
-        return [s], {k: st[k] for k in ("search_ms", "search_ms_device", "search_nodes", "passes", "launches")}
+        return [s], {k: st[k] for k in ("search_ms", "search_ms_device", "search_nodes", "passes", "launches",
+                                        "records", "handed_back")}
 
     def expansions(sols):
         tot = 0
@@ -726,6 +727,23 @@ def main():
                 "expansions_per_s_in_kernel": s_nodes / (s_ms / 1e3) if s_ms else None,
                 "expansions_per_s_in_kernel_timed_steps": dev_nodes / (dev_ms / 1e3) if dev_ms else None}
 
+    # HBM traffic of the frontiers and the hand-back queue (the only DRAM
+    # traffic of the method: a subtree's search stays in shared memory): each
+    # 24-byte record is written once and read once
+    rec_bytes = 24
+    fq_bytes = 2 * rec_bytes * sum(a["records"] + a["handed_back"] for a in agg_plain) / k
+    hbm_peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm_peak = float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        pass
+    fq_gbs = fq_bytes / (t_plain / k) / 1e9
+    hbm = {"bytes_per_step": fq_bytes, "gbs": fq_gbs, "peak_gbs": hbm_peak,
+           "frac": fq_gbs / hbm_peak if hbm_peak else None,
+           "what": "frontier records (splitter writes, first pass reads) and hand-back queue records, "
+                   "24 B each, written once and read once, plain form"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -765,6 +783,7 @@ def main():
             "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                        "reasons": clocks["reasons"]},
             "gpu_launches": launches * k,
+            "hbm_frontier_queue": hbm,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -374,3 +374,22 @@ def test_fused_iterations_24puzzle():
         rc, four = gpu_solve(5, tiles[lo:lo + 4])
         assert rc == bpida.OK
         check_against(5, tiles[lo:lo + 4], four, ref[lo:lo + 4])
+
+
+def test_first_solution_mode_one_board_per_call():
+    """First-solution mode, one board per call (the plain form): the length and
+    every non-final iteration exact, the final one at most the all-solutions
+    count, the moves an optimal solution."""
+    doc = _golden("perms15_100")
+    cheap = sorted(doc["instances"], key=lambda r: sum(r["nodes"]))[:12]
+    perms = I.perms15_100()
+    insts = I.walks15_16x40() + [perms[r["index"]] for r in cheap]
+    tiles = [x.tiles for x in insts]
+    ref = oracle.solve_batch(4, np.array(tiles, dtype=np.uint8), count_all=True)
+    for t, r in zip(tiles, ref):
+        rc, got = gpu_solve(4, [t], count_all=False)
+        g = got[0]
+        assert rc == bpida.OK and g["status"] == 0 and g["length"] == r.length
+        assert g["nodes"][:-1] == r.nodes[:-1]
+        assert 1 <= g["nodes"][-1] <= r.nodes[-1]
+        assert P.replay(4, t, g["moves"]) == list(range(16))
