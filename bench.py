@@ -753,10 +753,19 @@ def main():
         res = oracle.solve_batch(4, I.tiles_array([insts[i] for i in sample]), count_all=True, nthreads=cores)
         dt = time.perf_counter() - t0
         cn = sum(r.total_nodes for r in res)
+        # one thread (the paper's sequential-solver setting) on the cheapest
+        # boards up to ~1e8 nodes
+        one, _ = pick_cpu_sample(insts, gold, args.cpu_sample_nodes / 16)
+        t1 = time.perf_counter()
+        res1 = oracle.solve_batch(4, I.tiles_array([insts[i] for i in one]), count_all=True, nthreads=1)
+        dt1 = time.perf_counter() - t1
+        cn1 = sum(r.total_nodes for r in res1)
         cpu = {"value": cn / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "%d of %d boards (cheapest by stored oracle node count), %d expansions, %.1f s" % (
                    len(sample), n, cn, dt),
-               "instances_per_s": len(sample) / dt}
+               "instances_per_s": len(sample) / dt,
+               "single_thread": {"value": cn1 / dt1, "unit": UNIT, "cores": 1,
+                                 "sample": "%d cheapest boards, %d expansions, %.1f s" % (len(one), cn1, dt1)}}
 
     if rank == 0:
         line = {
