@@ -67,6 +67,17 @@ def _load():
         lib.oracle_manhattan_batch.restype = None
         lib.oracle_is_solvable_batch.argtypes = [ctypes.c_int, u8p, ctypes.c_int, i32p]
         lib.oracle_is_solvable_batch.restype = None
+        lib.oracle_pdb_table_bytes.argtypes = [ctypes.c_int]
+        lib.oracle_pdb_table_bytes.restype = ctypes.c_uint64
+        lib.oracle_pdb_build.argtypes = [ctypes.c_int, i32p, ctypes.c_int, u8p, ctypes.c_uint64, i32p]
+        lib.oracle_pdb_build.restype = ctypes.c_int
+        lib.oracle_pdb_h_batch.argtypes = [ctypes.c_int, i32p, u8p, u8p, ctypes.c_int, i32p]
+        lib.oracle_pdb_h_batch.restype = ctypes.c_int
+        lib.oracle_ida_pdb_batch.argtypes = [
+            ctypes.c_int, i32p, u8p, u8p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+            ctypes.c_int, ctypes.c_int, i32p, u8p, u64p, i32p, i32p, u64p, i32p, i32p,
+        ]
+        lib.oracle_ida_pdb_batch.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -93,8 +104,9 @@ def _ptr(a, ct):
 
 
 def solve_batch(W: int, tiles, count_all: bool = True, node_budget: int = 0,
-                nthreads: int = 0) -> List[OracleResult]:
-    """Solve every board (rows of ``tiles``, shape (n, W*W)) independently."""
+                nthreads: int = 0, pdb: "PatternDb" = None) -> List[OracleResult]:
+    """Solve every board (rows of ``tiles``, shape (n, W*W)) independently,
+    with the Manhattan distance or, given ``pdb``, its pattern databases."""
     lib = _load()
     t = np.ascontiguousarray(np.asarray(tiles, dtype=np.uint8).reshape(-1, W * W))
     n = t.shape[0]
@@ -109,15 +121,23 @@ def solve_batch(W: int, tiles, count_all: bool = True, node_budget: int = 0,
     out_status = np.zeros(n, np.int32)
     if nthreads <= 0:
         nthreads = os.cpu_count() or 1
-    if n:
-        rc = lib.oracle_ida_batch(
-            W, _ptr(t, ctypes.c_uint8), n, 1 if count_all else 0, node_budget, mi, ml, nthreads,
-            _ptr(out_len, ctypes.c_int), _ptr(out_moves, ctypes.c_uint8),
+    outs = (_ptr(out_len, ctypes.c_int), _ptr(out_moves, ctypes.c_uint8),
             _ptr(out_nodes, ctypes.c_uint64), _ptr(out_limits, ctypes.c_int),
             _ptr(out_iters, ctypes.c_int), _ptr(out_sol, ctypes.c_uint64),
             _ptr(out_h0, ctypes.c_int), _ptr(out_status, ctypes.c_int))
+    if n and pdb is None:
+        rc = lib.oracle_ida_batch(
+            W, _ptr(t, ctypes.c_uint8), n, 1 if count_all else 0, node_budget, mi, ml, nthreads, *outs)
         if rc != OK:
             raise ValueError("oracle_ida_batch rejected its arguments (code %d)" % rc)
+    elif n:
+        if pdb.W != W:
+            raise ValueError("pattern databases built for width %d" % pdb.W)
+        rc = lib.oracle_ida_pdb_batch(
+            W, _ptr(pdb.group_of_tile, ctypes.c_int), _ptr(pdb.concatenated, ctypes.c_uint8),
+            _ptr(t, ctypes.c_uint8), n, 1 if count_all else 0, node_budget, mi, ml, nthreads, *outs)
+        if rc != OK:
+            raise ValueError("oracle_ida_pdb_batch rejected its arguments (code %d)" % rc)
     res = []
     for i in range(n):
         it = int(out_iters[i])
@@ -131,8 +151,9 @@ def solve_batch(W: int, tiles, count_all: bool = True, node_budget: int = 0,
     return res
 
 
-def solve(W: int, tiles: Sequence[int], count_all: bool = True, node_budget: int = 0) -> OracleResult:
-    return solve_batch(W, [list(tiles)], count_all, node_budget, nthreads=1)[0]
+def solve(W: int, tiles: Sequence[int], count_all: bool = True, node_budget: int = 0,
+          pdb: "PatternDb" = None) -> OracleResult:
+    return solve_batch(W, [list(tiles)], count_all, node_budget, nthreads=1, pdb=pdb)[0]
 
 
 def is_solvable(W: int, tiles: Sequence[int]) -> bool:
@@ -157,3 +178,53 @@ def is_solvable_batch(W: int, tiles) -> np.ndarray:
     out = np.zeros(t.shape[0], np.int32)
     _load().oracle_is_solvable_batch(W, _ptr(t, ctypes.c_uint8), t.shape[0], _ptr(out, ctypes.c_int))
     return out.astype(bool)
+
+
+class PatternDb:
+    """Additive disjoint pattern databases built by the oracle (see the
+    "pattern databases" section of ``ida_oracle.c``): ``groups`` lists the
+    tiles of each group; every tile 1..W*W-1 belongs to exactly one group of
+    1 to 6 tiles. ``tables[g]`` holds d_G at index
+    sum_j pos(t_j) << 4j | blank << 4k (tiles of the group in increasing
+    order), 255 where no abstract state has that index."""
+
+    def __init__(self, W: int, groups: Sequence[Sequence[int]]):
+        lib = _load()
+        self.W = W
+        self.groups = [sorted(int(t) for t in g) for g in groups]
+        got = np.full(W * W, -1, np.int32)
+        for gi, g in enumerate(self.groups):
+            for t in g:
+                if not 1 <= t < W * W or got[t] != -1:
+                    raise ValueError("tile %d is out of range or in two groups" % t)
+                got[t] = gi
+        if (got[1:] < 0).any():
+            raise ValueError("every tile must belong to a group")
+        got[0] = 0
+        self.group_of_tile = got
+        self.tables = []
+        self.max_values = []
+        for gi, g in enumerate(self.groups):
+            size = int(lib.oracle_pdb_table_bytes(len(g)))
+            if size == 0:
+                raise ValueError("groups hold 1 to 6 tiles")
+            tab = np.empty(size, np.uint8)
+            mx = np.zeros(1, np.int32)
+            rc = lib.oracle_pdb_build(W, _ptr(got, ctypes.c_int), gi, _ptr(tab, ctypes.c_uint8), size,
+                                      _ptr(mx, ctypes.c_int))
+            if rc != OK:
+                raise ValueError("oracle_pdb_build failed (code %d)" % rc)
+            self.tables.append(tab)
+            self.max_values.append(int(mx[0]))
+        self.concatenated = np.ascontiguousarray(np.concatenate(self.tables))
+
+    def h_batch(self, tiles) -> np.ndarray:
+        """The heuristic value of every board (rows of W*W tiles)."""
+        t = np.ascontiguousarray(np.asarray(tiles, dtype=np.uint8).reshape(-1, self.W * self.W))
+        out = np.zeros(t.shape[0], np.int32)
+        rc = _load().oracle_pdb_h_batch(self.W, _ptr(self.group_of_tile, ctypes.c_int),
+                                        _ptr(self.concatenated, ctypes.c_uint8), _ptr(t, ctypes.c_uint8),
+                                        t.shape[0], _ptr(out, ctypes.c_int))
+        if rc != OK:
+            raise ValueError("oracle_pdb_h_batch failed (code %d)" % rc)
+        return out

@@ -146,3 +146,92 @@ def tree_size(W: int, tiles: Sequence[int], limit: int) -> Tuple[int, int]:
     res = T(tuple(tiles), 0, -1)
     T.cache_clear()
     return res
+
+
+def pattern_distances(W: int, group: Sequence[int]) -> Dict[Tuple[Tuple[int, ...], int], int]:
+    """Abstract distances of one pattern group, by a 0-1 breadth-first search
+    (deque: cost-0 successors go to the front, cost-1 ones to the back).
+
+    An abstract state is (positions of the group's tiles in increasing tile
+    order, blank position); the blank swaps with an adjacent cell, which
+    costs 1 if the cell holds one of the group's tiles and 0 otherwise. The
+    search starts at the abstract goal (tile t at cell t, blank at 0)."""
+    tiles = sorted(group)
+    start = (tuple(tiles), 0)
+    dist = {start: 0}
+    dq = deque([start])
+    done = set()
+    while dq:
+        s = dq.popleft()
+        if s in done:
+            continue
+        done.add(s)
+        pos, b = s
+        r, c = divmod(b, W)
+        for m in range(4):
+            dr, dc = DELTA_ROWCOL[m]
+            rr, cc = r + dr, c + dc
+            if not (0 <= rr < W and 0 <= cc < W):
+                continue
+            q = rr * W + cc
+            if q in pos:
+                j = pos.index(q)
+                n = (pos[:j] + (b,) + pos[j + 1:], q)
+                w = 1
+            else:
+                n = (pos, q)
+                w = 0
+            nd = dist[s] + w
+            if nd < dist.get(n, 1 << 30):
+                dist[n] = nd
+                if w == 0:
+                    dq.appendleft(n)
+                else:
+                    dq.append(n)
+    return dist
+
+
+def pattern_h(W: int, groups: Sequence[Sequence[int]], tables: Sequence[dict], s: Sequence[int]) -> int:
+    """Sum over groups of the abstract distance of the board's abstraction."""
+    where = {v: p for p, v in enumerate(s)}
+    h = 0
+    for g, tab in zip(groups, tables):
+        h += tab[(tuple(where[t] for t in sorted(g)), where[0])]
+    return h
+
+
+def tree_size_h(W: int, tiles: Sequence[int], limit: int, h) -> Tuple[int, int, int]:
+    """tree_size with heuristic h(state); also returns the smallest f of a
+    pruned child (the next limit of IDA*), or None if nothing was pruned."""
+    goal = tuple(range(W * W))
+    sys.setrecursionlimit(max(10000, sys.getrecursionlimit()))
+    hc = {}
+
+    def H(s):
+        v = hc.get(s)
+        if v is None:
+            v = hc[s] = h(s)
+        return v
+
+    @lru_cache(maxsize=None)
+    def T(s, g, last):
+        if s == goal:
+            return 1, 1, None
+        nodes, goals, fmin = 1, 0, None
+        for m, c in neighbours(W, s):
+            if last >= 0 and m == 3 - last:
+                continue
+            f = g + 1 + H(c)
+            if f <= limit:
+                a, b, fm = T(c, g + 1, m)
+                nodes += a
+                goals += b
+            else:
+                fm = f
+            if fm is not None and (fmin is None or fm < fmin):
+                fmin = fm
+        return nodes, goals, fmin
+
+    res = T(tuple(tiles), 0, -1)
+    T.cache_clear()
+    return res
