@@ -289,6 +289,52 @@ void bpida_get_stats(bpida_stats *out);
 /* Free the calling device's workspace. */
 void bpida_release_workspace(void);
 
+/* ---- pattern-database heuristic ----
+ * Additive disjoint pattern databases, the memory-intensive heuristic that
+ * the paper's conclusion (Section 7) names as future work: kept in device
+ * memory and read by the search kernels through L2.
+ *
+ * Tiles 1 .. W*W-1 are split into disjoint groups. For a group G with tiles
+ * t_0 < ... < t_{k-1}, an abstract state is the positions of G's tiles and
+ * of the blank; an abstract move swaps the blank with an adjacent cell and
+ * costs 1 if that cell holds a tile of G, else 0. Table G holds, at index
+ * sum_j pos(t_j) << 4j | blank << 4k (16^(k+1) bytes), the cost of a
+ * cheapest abstract path to the abstract goal (tile t at cell t, blank at
+ * 0), and 255 at indices that are no abstract state. h(board) = sum over
+ * groups of the entry of the board's abstraction: admissible, consistent,
+ * of the parity of the Manhattan distance and never below it, so every
+ * convention above holds unchanged (limits still rise by exactly 2) and
+ * results differ from the Manhattan ones only in the per-iteration node
+ * counts, which are those of IDA* with this heuristic.
+ */
+typedef struct bpida_pdb bpida_pdb;
+
+/* Builds the tables on the current device (on `stream`; returns once they
+ * are built). width: 3 or 4. group_of_tile[t] (t = 1 .. W*W-1; entry 0 is
+ * ignored) is t's group, numbered from 0 without gaps; at most 6 groups of
+ * 1 to 6 tiles each (a 6-tile group's table is 256 MB). On success *out
+ * owns the tables until bpida_pdb_destroy. Errors: BPIDA_EINVAL (bad
+ * width or grouping), BPIDA_ENOMEM, BPIDA_ECUDA. */
+bpida_status bpida_pdb_create(int width, const int *group_of_tile, bpida_pdb **out, void *stream);
+void bpida_pdb_destroy(bpida_pdb *pdb);
+int bpida_pdb_groups(const bpida_pdb *pdb);
+/* Bytes of group `group`'s table (0 for a bad group) and its largest entry
+ * (-1 for a bad group). */
+uint64_t bpida_pdb_table_bytes(const bpida_pdb *pdb, int group);
+int bpida_pdb_max_value(const bpida_pdb *pdb, int group);
+/* Copies group `group`'s table into dst (host or device memory, at least
+ * bpida_pdb_table_bytes bytes) on `stream` and waits for the copy. */
+bpida_status bpida_pdb_copy_table(const bpida_pdb *pdb, int group, uint8_t *dst, uint64_t bytes, void *stream);
+
+/* bpida_solve_ex with the pattern-database heuristic `pdb` (built on the
+ * current device, for cfg->width; width 0 means the tables' width).
+ * cfg->variant must be 0 and cfg->stack_entries 0, 384 or 512; everything
+ * else (first-solution mode, node budgets, the graph and host drivers) is
+ * as in bpida_solve_ex. Returns BPIDA_EINVAL for a null or foreign pdb. */
+bpida_status bpida_solve_pdb(const bpida_config *cfg, const bpida_pdb *pdb, const uint64_t *boards, int n,
+                             int *out_len, uint8_t *out_moves, uint64_t *out_nodes_per_iter,
+                             int *out_num_iters, int *out_status, uint64_t *out_solutions, void *stream);
+
 const char *bpida_status_str(int status);
 
 #ifdef __cplusplus

@@ -25,6 +25,8 @@ EXPORTS = (
     "bpida_get_stats", "bpida_release_workspace", "bpida_status_str", "bpida_solve_noalloc",
     "bpida_server_create", "bpida_server_submit", "bpida_server_poll", "bpida_server_in_flight",
     "bpida_server_get_stats", "bpida_server_clock", "bpida_server_set_time_slice", "bpida_server_destroy",
+    "bpida_pdb_create", "bpida_pdb_destroy", "bpida_pdb_groups", "bpida_pdb_table_bytes",
+    "bpida_pdb_max_value", "bpida_pdb_copy_table", "bpida_solve_pdb",
 )
 NOALLOC_MAX_BOARDS = 256
 
@@ -159,6 +161,20 @@ def load():
         lib.bpida_server_destroy.restype = None
         lib.bpida_status_str.argtypes = [ctypes.c_int]
         lib.bpida_status_str.restype = ctypes.c_char_p
+        lib.bpida_pdb_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(vp), vp]
+        lib.bpida_pdb_create.restype = ctypes.c_int
+        lib.bpida_pdb_destroy.argtypes = [vp]
+        lib.bpida_pdb_destroy.restype = None
+        lib.bpida_pdb_groups.argtypes = [vp]
+        lib.bpida_pdb_groups.restype = ctypes.c_int
+        lib.bpida_pdb_table_bytes.argtypes = [vp, ctypes.c_int]
+        lib.bpida_pdb_table_bytes.restype = ctypes.c_uint64
+        lib.bpida_pdb_max_value.argtypes = [vp, ctypes.c_int]
+        lib.bpida_pdb_max_value.restype = ctypes.c_int
+        lib.bpida_pdb_copy_table.argtypes = [vp, ctypes.c_int, vp, ctypes.c_uint64, vp]
+        lib.bpida_pdb_copy_table.restype = ctypes.c_int
+        lib.bpida_solve_pdb.argtypes = [ctypes.POINTER(Config), vp, vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
+        lib.bpida_solve_pdb.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -228,13 +244,14 @@ def make_config(width: int = 4, split_target: int = 0, warps_per_block: int = 0,
 
 
 def solve(boards: torch.Tensor, width: int = 4, config: Optional[Config] = None,
-          stream: Optional[torch.cuda.Stream] = None) -> Solution:
+          stream: Optional[torch.cuda.Stream] = None, pdb: Optional["PatternDb"] = None) -> Solution:
     """Solve packed boards already on the GPU.
 
     ``boards``: CUDA int64 tensor, shape (n,) for width 3/4, (n, 2) for 5,
     holding the packed words (bit pattern of the uint64 layout in bpida.h).
     Outputs are allocated on the same device; the call runs on ``stream``
-    (default: the current stream).
+    (default: the current stream). With ``pdb`` the heuristic is that
+    pattern database (bpida_solve_pdb), else the Manhattan distance.
     """
     lib = load()
     if not boards.is_cuda:
@@ -256,10 +273,13 @@ def solve(boards: torch.Tensor, width: int = 4, config: Optional[Config] = None,
     out_status = torch.empty(n, dtype=torch.int32, device=dev)
     out_sol = torch.empty(n, dtype=torch.int64, device=dev)
     s = stream if stream is not None else torch.cuda.current_stream(dev)
+    outs = (out_len.data_ptr(), out_moves.data_ptr(), out_nodes.data_ptr(), out_iters.data_ptr(),
+            out_status.data_ptr(), out_sol.data_ptr(), s.cuda_stream)
     with torch.cuda.device(dev):
-        rc = lib.bpida_solve_ex(ctypes.byref(cfg), boards.data_ptr(), n, out_len.data_ptr(),
-                                out_moves.data_ptr(), out_nodes.data_ptr(), out_iters.data_ptr(),
-                                out_status.data_ptr(), out_sol.data_ptr(), s.cuda_stream)
+        if pdb is None:
+            rc = lib.bpida_solve_ex(ctypes.byref(cfg), boards.data_ptr(), n, *outs)
+        else:
+            rc = lib.bpida_solve_pdb(ctypes.byref(cfg), pdb.handle, boards.data_ptr(), n, *outs)
     return Solution(rc, out_len, out_moves, out_nodes, out_iters, out_status, out_sol)
 
 
@@ -300,6 +320,62 @@ def solve_noalloc(boards: torch.Tensor, stream: Optional[torch.cuda.Stream] = No
                                      out_nodes.data_ptr(), out_iters.data_ptr(), out_status.data_ptr(),
                                      s.cuda_stream)
     return Solution(rc, out_len, out_moves, out_nodes, out_iters, out_status)
+
+
+class PatternDb:
+    """Pattern databases built on the GPU by bpida_pdb_create (see bpida.h):
+    ``groups`` lists the tiles of each group (every tile 1..W*W-1 in exactly
+    one group; at most 6 groups of 1 to 6 tiles)."""
+
+    def __init__(self, width: int, groups, device: Optional[torch.device] = None):
+        lib = load()
+        self.width = width
+        self.groups = [sorted(int(t) for t in g) for g in groups]
+        got = (ctypes.c_int * (width * width))()
+        seen = set()
+        for gi, g in enumerate(self.groups):
+            for t in g:
+                if not 1 <= t < width * width or t in seen:
+                    raise ValueError("tile %d is out of range or in two groups" % t)
+                seen.add(t)
+                got[t] = gi
+        if len(seen) != width * width - 1:
+            raise ValueError("every tile must belong to a group")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = lib.bpida_pdb_create(width, got, ctypes.byref(h), torch.cuda.current_stream(self.device).cuda_stream)
+        if rc != OK:
+            raise RuntimeError("bpida_pdb_create failed: %s" % status_str(rc))
+        self.handle = h.value
+
+    def table_bytes(self, group: int) -> int:
+        return int(load().bpida_pdb_table_bytes(self.handle, group))
+
+    def max_value(self, group: int) -> int:
+        return int(load().bpida_pdb_max_value(self.handle, group))
+
+    def table(self, group: int) -> torch.Tensor:
+        """Group ``group``'s table copied to a host uint8 tensor."""
+        out = torch.empty(self.table_bytes(group), dtype=torch.uint8)
+        with torch.cuda.device(self.device):
+            rc = load().bpida_pdb_copy_table(self.handle, group, out.data_ptr(), out.numel(),
+                                             torch.cuda.current_stream(self.device).cuda_stream)
+        if rc != OK:
+            raise RuntimeError("bpida_pdb_copy_table failed: %s" % status_str(rc))
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            with torch.cuda.device(self.device):
+                load().bpida_pdb_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Server:

@@ -8,8 +8,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libbpida.so")
 SOURCES = [os.path.join(HERE, "csrc", n) for n in ("bpida.cu", "bpida_noalloc.cu", "bpida_server.cu",
-                                                   "bpida_thread.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", n) for n in ("bpida_device.cuh", "bpida_thread.h")] + [
+                                                   "bpida_thread.cu", "bpida_pdb.cu")]
+DEPS = SOURCES + [os.path.join(HERE, "csrc", n) for n in ("bpida_device.cuh", "bpida_thread.h", "bpida_pdb.h")] + [
     os.path.join(ROOT, "include", "bpida.h")]
 
 NVCC_FLAGS = [

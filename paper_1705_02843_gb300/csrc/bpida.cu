@@ -20,6 +20,7 @@
 // search launch with CUDA events.
 #include "bpida.h"
 #include "bpida_device.cuh"
+#include "bpida_pdb.h"
 #include "bpida_thread.h"
 
 #include <algorithm>
@@ -45,8 +46,8 @@ struct DevBuf {
 };
 
 // W, S, warps per block, n, frontier cap, hand-back percentage, min rounds, min pass time, variant,
-// fused iterations
-typedef std::tuple<int, int, int, int, int, int, int, int, int, int> PlanKey;
+// fused iterations, pattern databases (their id; 0 = Manhattan distance)
+typedef std::tuple<int, int, int, int, int, int, int, int, int, int, unsigned long long> PlanKey;
 
 struct Plan {
     cudaGraph_t graph = nullptr;
@@ -149,6 +150,7 @@ Workspace *workspace_for(int dev)
 struct Settings {
     int width, count_all, split_target, wpb, S, exit_pct, min_rounds, driver, min_pass_ns, variant;
     uint64_t budget;
+    const bpida_pdb *pdb;  // pattern databases, or null (Manhattan distance)
 };
 
 // A step fuses the next iterations of an instance while the highest of them
@@ -206,14 +208,17 @@ struct Geometry {
     bool fuse;
 };
 
-template <int W, int S> void (*search_kernel(int variant, bool fuse))(const Dev<W>)
+template <int W, int S, bool PDB> void (*search_kernel(int variant, bool fuse))(const Dev<W>)
 {
-    return variant == 1 ? k_search_paper<W, S> : fuse ? k_search<W, S, true> : k_search<W, S, false>;
+    if constexpr (PDB)
+        return fuse ? k_search<W, S, true, true> : k_search<W, S, false, true>;
+    else
+        return variant == 1 ? k_search_paper<W, S> : fuse ? k_search<W, S, true> : k_search<W, S, false>;
 }
 
 // The whole solve as one graph (k_set_desc is launched before it):
 //   init -> WHILE(step){ split -> WHILE(pass){ search } -> advance } -> finalize
-template <int W, int S>
+template <int W, int S, bool PDB>
 cudaError_t build_graph(Plan &pl, Dev<W> d, const Geometry &g, const char **where)
 {
     cudaGraph_t G;
@@ -233,7 +238,7 @@ cudaError_t build_graph(Plan &pl, Dev<W> d, const Geometry &g, const char **wher
     const dim3 g_inst((g.n_cap + 127) / 128), g_prob(g.n_cap);
     cudaGraphNode_t n_init, n_step, n_fin;
     *where = "init/step/finalize nodes";
-    if ((e = add_kernel(&n_init, G, nullptr, 0, k_init<W>, g_inst, b128, 0, d)) != cudaSuccess)
+    if ((e = add_kernel(&n_init, G, nullptr, 0, k_init<W, PDB>, g_inst, b128, 0, d)) != cudaSuccess)
         return e;
     cudaGraph_t B;
     if ((e = add_while(&n_step, G, &n_init, 1, hs, &B)) != cudaSuccess)
@@ -247,7 +252,7 @@ cudaError_t build_graph(Plan &pl, Dev<W> d, const Geometry &g, const char **wher
     d.h_pass = hp;
     cudaGraphNode_t n_split, n_pass, n_adv;
     *where = "split/pass/advance nodes";
-    if ((e = add_kernel(&n_split, B, nullptr, 0, k_split<W>, g_prob, bsplit, 0, d)) != cudaSuccess)
+    if ((e = add_kernel(&n_split, B, nullptr, 0, k_split<W, PDB>, g_prob, bsplit, 0, d)) != cudaSuccess)
         return e;
     cudaGraph_t P;
     if ((e = add_while(&n_pass, B, &n_split, 1, hp, &P)) != cudaSuccess)
@@ -257,14 +262,14 @@ cudaError_t build_graph(Plan &pl, Dev<W> d, const Geometry &g, const char **wher
 
     cudaGraphNode_t n_search;
     *where = "search node";
-    if ((e = add_kernel(&n_search, P, nullptr, 0, search_kernel<W, S>(g.variant, g.fuse), dim3(g.grid), dim3(g.threads),
+    if ((e = add_kernel(&n_search, P, nullptr, 0, search_kernel<W, S, PDB>(g.variant, g.fuse), dim3(g.grid), dim3(g.threads),
                         g.smem, d)) != cudaSuccess)
         return e;
     *where = "cudaGraphInstantiate";
     return cudaGraphInstantiate(&pl.exec, G, 0);
 }
 
-template <int W, int S>
+template <int W, int S, bool PDB = false>
 bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_len, uint8_t *out_moves,
                  uint64_t *out_nodes, int *out_iters, int *out_status, uint64_t *out_solutions, cudaStream_t st)
 {
@@ -294,16 +299,16 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
         int optin = 0;
         cudaFuncAttributes fa;
         CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        CK(cudaFuncGetAttributes(&fa, search_kernel<W, S>(cfg.variant, fuse)));
+        CK(cudaFuncGetAttributes(&fa, search_kernel<W, S, PDB>(cfg.variant, fuse)));
         lim = optin - (int)fa.sharedSizeBytes;
-        CK(cudaFuncSetAttribute(search_kernel<W, S>(cfg.variant, fuse), cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        CK(cudaFuncSetAttribute(search_kernel<W, S, PDB>(cfg.variant, fuse), cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     }
     if (g.smem > (size_t)lim)
         return BPIDA_EINVAL;
     static std::map<std::tuple<int, int, int, int>, int> occ;
     int &bpsm = occ[std::make_tuple(dev, wpb, cfg.variant, fuse ? 1 : 0)];
     if (bpsm == 0)
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, search_kernel<W, S>(cfg.variant, fuse), g.threads, g.smem));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, search_kernel<W, S, PDB>(cfg.variant, fuse), g.threads, g.smem));
     if (bpsm < 1)
         return BPIDA_EINVAL;
     g.grid = sms * bpsm;
@@ -390,6 +395,11 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     d.tune.growth = 8;
     d.tune.min_pass_ns = cfg.min_pass_ns;
     d.lut = make_move_lut<W>();
+    if constexpr (PDB) {
+        d.pdb.tab = cfg.pdb->tab;
+        d.pdb.info = cfg.pdb->d_info;
+        d.pdb.goal = cfg.pdb->goal;
+    }
 
     CallDesc desc;
     std::memset(&desc, 0, sizeof desc);
@@ -416,13 +426,13 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     const dim3 g_inst((n + 127) / 128);
     if (cfg.driver == 0) {
         const PlanKey key(W, S, cfg.wpb, n, g.tcap, cfg.exit_pct, cfg.min_rounds, cfg.min_pass_ns, cfg.variant,
-                          fuse ? 1 : 0);
+                          fuse ? 1 : 0, PDB ? cfg.pdb->id : 0ull);
         auto found = ws.plans.find(key);
         if (found == ws.plans.end() || !found->second.exec || found->second.gen != ws.gen) {
             ws.trim_plans();
             Plan &pl = ws.plans[key];
             const char *where = "";
-            cudaError_t e = build_graph<W, S>(pl, d, g, &where);
+            cudaError_t e = build_graph<W, S, PDB>(pl, d, g, &where);
             if (e != cudaSuccess) {
                 std::fprintf(stderr, "bpida: graph build failed at %s: %s\n", where, cudaGetErrorString(e));
                 pl.destroy();
@@ -441,20 +451,20 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     } else {
         // host-driven loop over the same kernels
         d.graph = 0;
-        k_init<W><<<g_inst, b128, 0, st>>>(d);
+        k_init<W, PDB><<<g_inst, b128, 0, st>>>(d);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(ws.h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         stats.launches = 2;
         int n_active = ws.h_ctrl->n_active;
         while (n_active > 0) {
-            k_split<W><<<n_active, bsplit, 0, st>>>(d);
+            k_split<W, PDB><<<n_active, bsplit, 0, st>>>(d);
             CK(cudaGetLastError());
             stats.launches += 1;
             for (;;) {
                 if (g_timing)
                     CK(cudaEventRecord(ws.ev0, st));
-                search_kernel<W, S>(cfg.variant, fuse)<<<g.grid, g.threads, g.smem, st>>>(d);
+                search_kernel<W, S, PDB>(cfg.variant, fuse)<<<g.grid, g.threads, g.smem, st>>>(d);
                 CK(cudaGetLastError());
                 if (g_timing)
                     CK(cudaEventRecord(ws.ev1, st));
@@ -503,6 +513,18 @@ template <int W>
 bpida_status run_w(const Settings &cfg, const uint64_t *boards, int n, int *out_len, uint8_t *out_moves,
                    uint64_t *out_nodes, int *out_iters, int *out_status, uint64_t *out_sol, cudaStream_t st)
 {
+    if (cfg.pdb) {
+        // pattern databases: 8- and 15-puzzle, stacks of 384 or 512 entries
+        if constexpr (W <= 4) {
+            if (cfg.S == 384)
+                return run<W, 384, true>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status,
+                                         out_sol, st);
+            if (cfg.S == 512)
+                return run<W, 512, true>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status,
+                                         out_sol, st);
+        }
+        return BPIDA_EINVAL;
+    }
     switch (cfg.S) {
     case 256: return run<W, 256>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, out_sol, st);
     case 384: return run<W, 384>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, out_sol, st);
@@ -537,11 +559,13 @@ int bpida_max_iters(int width)
     return 0;
 }
 
-bpida_status bpida_solve_ex(const bpida_config *cfg_in, const uint64_t *boards, int n, int *out_len,
-                            uint8_t *out_moves, uint64_t *out_nodes_per_iter, int *out_num_iters,
-                            int *out_status, uint64_t *out_solutions, void *stream)
+}  // extern "C"
+
+namespace {
+
+// Reads a config (null: defaults) and checks what the host can check.
+bpida_status parse_settings(const bpida_config *cfg_in, int n, Settings &cfg)
 {
-    Settings cfg;
     cfg.width = (cfg_in && cfg_in->width) ? cfg_in->width : 4;
     cfg.count_all = cfg_in ? cfg_in->count_all : 1;
     cfg.split_target = cfg_in ? cfg_in->split_target : 0;
@@ -554,6 +578,7 @@ bpida_status bpida_solve_ex(const bpida_config *cfg_in, const uint64_t *boards, 
     cfg.min_pass_ns = (cfg_in && cfg_in->min_pass_us != 0) ? (cfg_in->min_pass_us < 0 ? 0 : cfg_in->min_pass_us * 1000)
                                                              : 10000;
     cfg.budget = cfg_in ? cfg_in->node_budget : 0;
+    cfg.pdb = nullptr;
     if (cfg.width < 3 || cfg.width > 5 || n < 0)
         return BPIDA_EINVAL;
     if (cfg.S != 256 && cfg.S != 384 && cfg.S != 480 && cfg.S != 512 && cfg.S != 768 && cfg.S != 1024)
@@ -568,6 +593,38 @@ bpida_status bpida_solve_ex(const bpida_config *cfg_in, const uint64_t *boards, 
         return BPIDA_EINVAL;
     if (cfg.count_all != 0 && cfg.count_all != 1)
         return BPIDA_EINVAL;
+    return BPIDA_OK;
+}
+
+bpida_status dispatch(const Settings &cfg, const uint64_t *boards, int n, int *out_len, uint8_t *out_moves,
+                      uint64_t *out_nodes_per_iter, int *out_num_iters, int *out_status, uint64_t *out_solutions,
+                      cudaStream_t st)
+{
+    switch (cfg.width) {
+    case 3:
+        return run_w<3>(cfg, boards, n, out_len, out_moves, out_nodes_per_iter, out_num_iters, out_status,
+                        out_solutions, st);
+    case 4:
+        return run_w<4>(cfg, boards, n, out_len, out_moves, out_nodes_per_iter, out_num_iters, out_status,
+                        out_solutions, st);
+    default:
+        return run_w<5>(cfg, boards, n, out_len, out_moves, out_nodes_per_iter, out_num_iters, out_status,
+                        out_solutions, st);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+bpida_status bpida_solve_ex(const bpida_config *cfg_in, const uint64_t *boards, int n, int *out_len,
+                            uint8_t *out_moves, uint64_t *out_nodes_per_iter, int *out_num_iters,
+                            int *out_status, uint64_t *out_solutions, void *stream)
+{
+    Settings cfg;
+    const bpida_status bad = parse_settings(cfg_in, n, cfg);
+    if (bad != BPIDA_OK)
+        return bad;
     if (n == 0)
         return BPIDA_OK;
     if (!boards || !out_len || !out_moves || !out_nodes_per_iter)
@@ -586,17 +643,45 @@ bpida_status bpida_solve_ex(const bpida_config *cfg_in, const uint64_t *boards, 
         g_stats = stats;
         return r;
     }
-    switch (cfg.width) {
-    case 3:
-        return run_w<3>(cfg, boards, n, out_len, out_moves, out_nodes_per_iter, out_num_iters, out_status,
-                        out_solutions, st);
-    case 4:
-        return run_w<4>(cfg, boards, n, out_len, out_moves, out_nodes_per_iter, out_num_iters, out_status,
-                        out_solutions, st);
-    default:
-        return run_w<5>(cfg, boards, n, out_len, out_moves, out_nodes_per_iter, out_num_iters, out_status,
-                        out_solutions, st);
-    }
+    return dispatch(cfg, boards, n, out_len, out_moves, out_nodes_per_iter, out_num_iters, out_status,
+                    out_solutions, st);
+}
+
+bpida_status bpida_solve_pdb(const bpida_config *cfg_in, const bpida_pdb *pdb, const uint64_t *boards, int n,
+                             int *out_len, uint8_t *out_moves, uint64_t *out_nodes_per_iter, int *out_num_iters,
+                             int *out_status, uint64_t *out_solutions, void *stream)
+{
+    if (!pdb)
+        return BPIDA_EINVAL;
+    bpida_config c;
+    std::memset(&c, 0, sizeof c);
+    if (cfg_in)
+        c = *cfg_in;
+    else
+        c.count_all = 1;
+    if (c.width == 0)
+        c.width = pdb->width;
+    if (c.stack_entries != 0 && c.stack_entries != 384 && c.stack_entries != 512)
+        return BPIDA_EINVAL;
+    Settings cfg;
+    const bpida_status bad = parse_settings(&c, n, cfg);
+    if (bad != BPIDA_OK)
+        return bad;
+    if (cfg.variant != 0 || cfg.width != pdb->width)
+        return BPIDA_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return BPIDA_ECUDA;
+    if (dev != pdb->dev)
+        return BPIDA_EINVAL;
+    cfg.pdb = pdb;
+    if (n == 0)
+        return BPIDA_OK;
+    if (!boards || !out_len || !out_moves || !out_nodes_per_iter)
+        return BPIDA_EINVAL;
+    std::lock_guard<std::mutex> lock(g_mu);
+    return dispatch(cfg, boards, n, out_len, out_moves, out_nodes_per_iter, out_num_iters, out_status,
+                    out_solutions, (cudaStream_t)stream);
 }
 
 bpida_status bpida_solve(const uint64_t *boards, int n, int *out_len, uint8_t *out_moves,

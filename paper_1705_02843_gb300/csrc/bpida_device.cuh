@@ -285,6 +285,44 @@ struct Fuse {
                                    // steps saved are shared)
 };
 
+// Additive disjoint pattern databases: the memory-intensive heuristic that
+// the paper's conclusion names as future work (Section 7), kept in global
+// memory and read through L2. Tiles 1..N-1 are split into disjoint groups;
+// group G's table holds, for every placement of its tiles and of the blank,
+// the fewest moves of G's own tiles that bring G home (moves of other tiles
+// are free), at index sum_j pos(t_j) << 4j | blank << 4k (t_0 < ... < t_{k-1}
+// its tiles), and h is the sum over groups. A move changes one group's
+// value by exactly 1 and no other (the blank's position is part of every
+// entry), so h is consistent, has the parity of the Manhattan distance, and
+// the search's slack arithmetic (a child keeps slack s or drops to s - 2) is
+// the Manhattan one; only the direction of the step is read from a table.
+//
+// The search kernel works on the inverse board: 4-bit slot s holds the
+// position of the tile in slot s (slot 0: the blank; then the groups' tiles,
+// group by group, in increasing order), so a group's index is one field of
+// the inverse plus the blank's nibble. Stack entries stay 16 bytes: the
+// inverse takes the board's place and the metadata carries h_g mod 4 of
+// every group (enough to tell h_g + 1 from h_g - 1).
+static constexpr int PDB_MAX_GROUPS = 6;
+static constexpr int PDB_MAX_TILES = 6;    // per group: a table of 16^(k+1) bytes (256 MB at k = 6)
+static constexpr int PDB_VSHIFT = 20;      // stack metadata: h_g mod 4 at bits 20 + 2g
+static constexpr uint32_t PDB_VMASK = 0xFFF00000u;
+struct PdbInfo {
+    // per slot s >= 1: bits 0..7 the group's field offset in the inverse,
+    // 8..15 its width, 16..23 the metadata bit of h_g mod 4, 32..63 the
+    // byte offset of the group's table (slot 0: zero)
+    unsigned long long slot[16];
+    unsigned char slot_of_tile[16], tile_of_slot[16];
+    int ng;
+    int goff[PDB_MAX_GROUPS], gbits[PDB_MAX_GROUPS];
+    unsigned base[PDB_MAX_GROUPS];
+};
+struct PdbDev {
+    const unsigned char *tab;  // all groups' tables, one after another (null: Manhattan distance)
+    const PdbInfo *info;       // device copy of the layout
+    unsigned long long goal;   // the goal's inverse board
+};
+
 struct Tune {
     int min_rounds;      // rounds before a warp may hand its stack back
     int exit_threshold;  // warps that must have run dry first
@@ -379,6 +417,7 @@ template <int W> struct Dev {
     int slice;
     unsigned *carry;
     int *fbase, *fcount;
+    PdbDev pdb;                 // pattern databases (solve calls with a PDB heuristic)
 };
 
 __device__ __forceinline__ unsigned long long global_ns();
@@ -401,6 +440,64 @@ __device__ __forceinline__ unsigned long long global_ns()
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
+}
+
+// ---- pattern-database helpers ----
+// Copies the layout into shared memory (block-wide; a barrier follows).
+__device__ __forceinline__ void pdb_load_info(PdbInfo *dst, const PdbInfo *src)
+{
+    for (int i = threadIdx.x; i < (int)(sizeof(PdbInfo) / 4); i += blockDim.x)
+        ((unsigned *)dst)[i] = ((const unsigned *)src)[i];
+}
+// The inverse board of a position -> tile board.
+template <int W> __device__ __forceinline__ uint64_t pdb_inverse(uint64_t b, const PdbInfo &pi)
+{
+    uint64_t v = 0;
+#pragma unroll
+    for (int p = 0; p < Geo<W>::N; ++p)
+        v |= (uint64_t)p << (4 * pi.slot_of_tile[tile_at<W>(b, p)]);
+    return v;
+}
+// The position -> tile board of an inverse board.
+template <int W> __device__ __forceinline__ uint64_t pdb_board(uint64_t inv, const PdbInfo &pi)
+{
+    uint64_t b = 0;
+#pragma unroll
+    for (int s = 0; s < Geo<W>::N; ++s)
+        b |= (uint64_t)pi.tile_of_slot[s] << (4 * ((inv >> (4 * s)) & 15u));
+    return b;
+}
+// Table index of the group whose tiles sit in field [goff, goff + gbits).
+__device__ __forceinline__ uint32_t pdb_index(uint64_t inv, uint32_t goff, uint32_t gbits)
+{
+    return ((uint32_t)(inv >> goff) & ((1u << gbits) - 1u)) | (((uint32_t)inv & 15u) << gbits);
+}
+// h of an inverse board (vb: h_g mod 4 of every group, as in the stack metadata).
+__device__ __forceinline__ int pdb_h(const PdbDev &d, const PdbInfo &pi, uint64_t inv, uint32_t *vb)
+{
+    int h = 0;
+    uint32_t bits = 0;
+    for (int g = 0; g < pi.ng; ++g) {
+        const uint32_t v = d.tab[pi.base[g] + pdb_index(inv, (uint32_t)pi.goff[g], (uint32_t)pi.gbits[g])];
+        h += (int)v;
+        bits |= (v & 3u) << (PDB_VSHIFT + 2 * g);
+    }
+    if (vb)
+        *vb = bits;
+    return h;
+}
+// Whether sliding the tile at np into the blank at p raises h (else it
+// lowers h by 1); inv is the parent's inverse board.
+__device__ __forceinline__ bool pdb_away(const PdbDev &d, const PdbInfo &pi, uint64_t inv, uint32_t p, uint32_t np,
+                                         unsigned tile)
+{
+    const uint32_t j = pi.slot_of_tile[tile];
+    const unsigned long long inf = pi.slot[j];
+    const uint32_t goff = (uint32_t)inf & 255u, gbits = ((uint32_t)inf >> 8) & 255u;
+    const uint64_t dd = (uint64_t)(p ^ np);
+    const uint64_t child = inv ^ (dd << (4 * j)) ^ dd;
+    const unsigned char *t = d.tab + (inf >> 32);
+    return t[pdb_index(child, goff, gbits)] > t[pdb_index(inv, goff, gbits)];
 }
 
 // ---- warp stack entries ----
@@ -542,9 +639,11 @@ template <int W> __device__ __forceinline__ LutRow<W> lut_row_sh(const unsigned 
     return SharedLut<W>::row(base, (int)(sh / (uint32_t)Geo<W>::BITS));
 }
 
-template <int W, int S>
+// PDB: stack entries hold inverse boards; records hold boards.
+template <int W, int S, bool PDB = false>
 __device__ __forceinline__ void hand_back_stack(const Dev<W> &a, Rec<W> *out, const WarpStack<W> &stk,
-                                                int from, int k, unsigned inst, int lane)
+                                                int from, int k, unsigned inst, int lane,
+                                                const PdbInfo *pi = nullptr)
 {
     if (k <= 0)
         return;
@@ -562,7 +661,10 @@ __device__ __forceinline__ void hand_back_stack(const Dev<W> &a, Rec<W> *out, co
         uint32_t m, o;
         stk.get(from + j, b, m, o);
         Rec<W> r;
-        r.b = b;
+        if constexpr (PDB)
+            r.b = pdb_board<W>(b, *pi);
+        else
+            r.b = b;
         r.meta = rec_from_sm<W>(m);
         r.inst = inst;
         r.origin = o;
@@ -624,6 +726,16 @@ __device__ __forceinline__ void hand_back_records(const Dev<W> &a, bool frontier
 
 template <int W> __device__ void end_of_pass(const Dev<W> &a);
 
+// The goal as the search kernel stores boards (PDB: the inverse board).
+template <int W, bool PDB>
+__device__ __forceinline__ typename Geo<W>::B search_goal(const Dev<W> &a)
+{
+    if constexpr (PDB)
+        return (typename Geo<W>::B)a.pdb.goal;
+    else
+        return goal_board<W>();
+}
+
 // One warp = one shared stack (Algorithm 1's openList). Each round pops up
 // to 32 nodes (one per lane), tests them for the goal, and generates the
 // children of the rest; children with f <= limit are pushed at slots
@@ -633,7 +745,9 @@ template <int W> __device__ void end_of_pass(const Dev<W> &a);
 // warps have run dry, busy warps hand their open nodes to the next pass.
 // FUSE: the kernel also counts popped nodes and goals by slack for fused
 // iterations (see Fuse); without it that code is compiled out.
-template <int W, int S, bool FUSE = false>
+// PDB: the heuristic is the pattern databases' sum (stack entries hold
+// inverse boards and h_g mod 4; see PdbInfo), else the Manhattan distance.
+template <int W, int S, bool FUSE = false, bool PDB = false>
 __global__ void k_search(const Dev<W> a)
 {
     typedef typename Geo<W>::B B;
@@ -652,6 +766,13 @@ __global__ void k_search(const Dev<W> a)
         s_nodes = 0;
     }
     SharedLut<W>::load(lut, a.lut);
+    const PdbInfo *pi = nullptr;
+    if constexpr (PDB) {
+        static_assert(W <= 4, "pattern databases: 8- and 15-puzzle");
+        __shared__ PdbInfo s_pi;
+        pdb_load_info(&s_pi, a.pdb.info);
+        pi = &s_pi;
+    }
     __syncthreads();
     const Rec<W> *in = a.ctrl->qi ? a.q1 : a.q0;
     Rec<W> *out = a.ctrl->qi ? a.q0 : a.q1;
@@ -673,7 +794,7 @@ __global__ void k_search(const Dev<W> a)
     ovf.init(a.ovf + gwarp * (size_t)a.ovf_cap * WarpStack<W>::ENTRY_BYTES, a.ovf_cap);
     int ovf_n = 0;
     const unsigned lt = (1u << lane) - 1u;
-    const B GOAL = goal_board<W>();
+    const B GOAL = search_goal<W, PDB>(a);
     const int n_in = a.ctrl->n_in;
     const int total_warps = gridDim.x * (blockDim.x >> 5);
     const int chunk = max(1, min(32, n_in / (total_warps * 4)));
@@ -736,8 +857,16 @@ __global__ void k_search(const Dev<W> a)
             const bool budgeted = left != ~0ull;
             const bool watch = budgeted || first_only;
             const bool dropped = watch && *(volatile unsigned *)&a.cnt.aborted[inst0];
-            if (lane < cnt && !dropped)
-                stk.put(lane, r.b, sm_from_rec<W>(r.meta), r.origin);
+            if (lane < cnt && !dropped) {
+                if constexpr (PDB) {
+                    const uint64_t inv = pdb_inverse<W>(r.b, *pi);
+                    uint32_t vb;
+                    pdb_h(a.pdb, *pi, inv, &vb);
+                    stk.put(lane, inv, sm_from_rec<W>(r.meta) | vb, r.origin);
+                } else {
+                    stk.put(lane, r.b, sm_from_rec<W>(r.meta), r.origin);
+                }
+            }
             int top = dropped ? 0 : cnt;
             if (inst0 != acc_inst) {
                 publish();
@@ -781,7 +910,7 @@ __global__ void k_search(const Dev<W> a)
                         }
                         ovf_n += k;
                     } else {
-                        hand_back_stack<W, S>(a, out, stk, 0, k, inst0, lane);
+                        hand_back_stack<W, S, PDB>(a, out, stk, 0, k, inst0, lane, pi);
                     }
                     __syncwarp();
                     for (int j0 = 0; j0 < top - k; j0 += 32) {
@@ -839,9 +968,55 @@ __global__ void k_search(const Dev<W> a)
                 const unsigned allowed = (act && !goal) ? (LegalMoves<W>::at_sh(sh_p) & ~((mt >> 7) & 15u)) : 0u;
                 const bool low = s < 2;
                 const uint32_t sbase = mt & (255u << 11);
-                const LutRow<W> row = lut_row_sh<W>(lut, sh_p);
                 bool pruned = false;
                 int base = top;
+                if constexpr (PDB) {
+                    // b is the inverse board; the step's direction comes from
+                    // the moved tile's group table, h_g mod 4 from the metadata
+                    const uint32_t vkeep = mt & PDB_VMASK;
+                    bool bad = false;
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const bool legal = (allowed >> m) & 1u;
+                        const uint32_t sh_np = sh_p + (uint32_t)(4 * move_off<W>(m));
+                        const uint32_t np = sh_np >> 2;
+                        // slot of the tile at np: the inverse's nibble equal to
+                        // np (bit 3 of each zero nibble of b ^ np...np; slot 0
+                        // holds the blank, which is not at np)
+                        const uint32_t rep = np * 0x11111111u;
+                        const uint32_t xl = (uint32_t)b ^ rep, xh = (uint32_t)(b >> 32) ^ rep;
+                        const uint32_t zl = ~(((xl & 0x77777777u) + 0x77777777u) | xl | 0x77777777u);
+                        const uint32_t zh = ~(((xh & 0x77777777u) + 0x77777777u) | xh | 0x77777777u);
+                        const uint32_t j4 = zl ? (uint32_t)__ffs((int)zl) - 4u : (uint32_t)__ffs((int)zh) + 28u;
+                        const unsigned long long inf = pi->slot[(j4 >> 2) & 15u];
+                        // the tile moves np -> p, the blank p -> np
+                        const uint64_t dd = (uint64_t)((sh_p ^ sh_np) >> 2);
+                        const B child = b ^ (dd << j4) ^ dd;
+                        const uint32_t vsh = ((uint32_t)inf >> 16) & 255u;
+                        uint32_t v = 0;
+                        if (legal)
+                            v = __ldg(a.pdb.tab + (inf >> 32) +
+                                      pdb_index(child, (uint32_t)inf & 255u, ((uint32_t)inf >> 8) & 255u));
+                        const uint32_t vold = mt >> vsh;
+                        // h_g rose by 1 (dv = 1) or fell by 1 (dv = 3); any other
+                        // dv is an inconsistent table: it counts as a rise (so a
+                        // subtree stays finite) and fails the call
+                        const uint32_t dv = (v - vold) & 3u;
+                        const bool away = dv != 3u;
+                        bad |= legal && dv != 1u && dv != 3u;
+                        const bool push = legal && !(away && low);
+                        pruned |= legal && away && low;
+                        const uint32_t cm = ((sh_np + sbase + ((1u << (3 - m)) << 7)) - (away ? (2u << 11) : 0u)) |
+                                            (vkeep ^ (((v ^ vold) & 3u) << vsh));
+                        const unsigned pm = __ballot_sync(FULL, push);
+                        if (push)
+                            stk.put(base + __popc(pm & lt), child, cm, org);
+                        base += __popc(pm);
+                    }
+                    if (__any_sync(FULL, bad) && lane == 0)
+                        atomicOr(&a.ctrl->err, ERR_INTERNAL);
+                } else {
+                const LutRow<W> row = lut_row_sh<W>(lut, sh_p);
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
                     const bool legal = (allowed >> m) & 1u;
@@ -860,6 +1035,7 @@ __global__ void k_search(const Dev<W> a)
                     if (push)
                         stk.put(base + __popc(pm & lt), child, cm, org);
                     base += __popc(pm);
+                }
                 }
                 top = base;
                 if (pruned)
@@ -917,9 +1093,9 @@ __global__ void k_search(const Dev<W> a)
             if (budgeted)
                 publish();
             if (stop) {
-                hand_back_stack<W, S>(a, out, stk, 0, top, inst0, lane);
+                hand_back_stack<W, S, PDB>(a, out, stk, 0, top, inst0, lane, pi);
                 if (OVF)
-                    hand_back_stack<W, S>(a, out, ovf, 0, ovf_n, inst0, lane);
+                    hand_back_stack<W, S, PDB>(a, out, ovf, 0, ovf_n, inst0, lane, pi);
                 ovf_n = 0;
                 hand_back_records<W>(a, frontier, n_act, n_front, act, in, out, i + cnt, end, lane);
                 // input that no warp has taken yet goes back too (a stop at
@@ -1143,7 +1319,7 @@ __device__ __forceinline__ bool last_block_done(unsigned *counter, int *s_last)
     return false;
 }
 
-template <int W>
+template <int W, bool PDB = false>
 __global__ void __launch_bounds__(SPLIT_THREADS) k_split(const Dev<W> a)
 {
     typedef typename Geo<W>::B B;
@@ -1171,6 +1347,12 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split(const Dev<W> a)
         }
     } else if (k < n_active) {
         SharedLut<W>::load(lut, a.lut);
+        const PdbInfo *pi = nullptr;
+        if constexpr (PDB) {
+            __shared__ PdbInfo s_pi;
+            pdb_load_info(&s_pi, a.pdb.info);
+            pi = &s_pi;
+        }
         const unsigned inst = inst_k;
         const InstState<W> st = a.state[inst];
         Rec<W> *A = a.scratch + region_of(a, k, inst);
@@ -1242,13 +1424,21 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split(const Dev<W> a)
                         atomicAdd(&s_low[s >> 1], 1u);
                     const uint32_t d = m_hi(r.meta);
                     const LutRow<W> e = SharedLut<W>::row(lut, p);
+                    uint64_t inv = 0;
+                    if constexpr (PDB)
+                        inv = pdb_inverse<W>(r.b, *pi);
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
                         if (!e.legal(m) || last == 3 - m)
                             continue;
                         const int np = p + move_off<W>(m);
                         const unsigned t = tile_at<W>(r.b, np);
-                        const int s2 = e.away(m, t) ? s - 2 : s;
+                        bool away;
+                        if constexpr (PDB)
+                            away = pdb_away(a.pdb, *pi, inv, (uint32_t)p, (uint32_t)np, t);
+                        else
+                            away = e.away(m, t);
+                        const int s2 = away ? s - 2 : s;
                         if (s2 < 0) {
                             fmin = min(fmin, -s2);
                             continue;
@@ -1600,7 +1790,7 @@ static __global__ void k_set_desc(CallDesc d, CallDesc *dst, Ctrl *ctrl)
 // Validates board b (permutation, parity class, h0 <= max length) and sets
 // up instance i: state, zeroed output rows. Returns true when the instance
 // is to be searched.
-template <int W>
+template <int W, bool PDB = false>
 __device__ bool init_instance(const Dev<W> &a, const CallDesc &dsc, int i, typename Geo<W>::B b)
 {
     typedef typename Geo<W>::B B;
@@ -1651,6 +1841,10 @@ __device__ bool init_instance(const Dev<W> &a, const CallDesc &dsc, int i, typen
         const int parity = (W & 1) ? (inv & 1) : ((inv + blank / W) & 1);
         ok = parity == 0;
     }
+    if constexpr (PDB) {
+        if (ok)
+            h = pdb_h(a.pdb, *a.pdb.info, pdb_inverse<W>(b, *a.pdb.info), nullptr);
+    }
     st.start_meta = 0;
     st.root_meta = 0;
     st.h0 = ok ? h : -1;
@@ -1699,14 +1893,14 @@ __device__ __forceinline__ typename Geo<W>::B load_board(const uint64_t *boards,
         return (B)boards[2 * i] | ((B)boards[2 * i + 1] << 64);
 }
 
-template <int W>
+template <int W, bool PDB = false>
 __global__ void k_init(const Dev<W> a)
 {
     __shared__ int s_last;
     const CallDesc dsc = *a.desc;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < dsc.n) {
-        if (init_instance<W>(a, dsc, i, load_board<W>(dsc.boards, i))) {
+        if (init_instance<W, PDB>(a, dsc, i, load_board<W>(dsc.boards, i))) {
             const int j = atomicAdd(&a.ctrl->n_active, 1);
             a.act0[j] = (unsigned)i;
         }

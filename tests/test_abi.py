@@ -61,3 +61,32 @@ def test_variant_arguments_are_checked_before_any_work(lib):
     for v in (bpida.PSIMPLE, bpida.PSTATICLB, bpida.PFULLLB):
         cfg = bpida.make_config(4, variant=v)
         assert b.bpida_solve_ex(ctypes.byref(cfg), None, 0, None, None, None, None, None, None, None) == bpida.OK
+
+
+def test_pattern_database_arguments_are_checked_before_any_work(lib):
+    """Bad widths and groupings, a null table set and null outputs are
+    rejected on the host, before any device call."""
+    b = bpida.load()
+    h = ctypes.c_void_p()
+    ok15 = [0] + [0] * 5 + [1] * 5 + [2] * 5
+    cases = [
+        (5, ok15 + [0] * 9),                       # 24-puzzle: not supported
+        (2, [0, 0, 0, 0]),                         # width out of range
+        (4, [0] + [0] * 7 + [1] * 8),              # a group of 8 tiles
+        (4, [0] + [0] * 5 + [2] * 10),             # group 1 empty
+        (4, [0] + [6] * 3 + [0] * 12),             # group index 6
+        (4, [0] + [-1] + [0] * 14),                # negative group
+    ]
+    for width, groups in cases:
+        arr = (ctypes.c_int * len(groups))(*groups)
+        assert b.bpida_pdb_create(width, arr, ctypes.byref(h), None) == bpida.EINVAL, (width, groups)
+        assert h.value is None
+    assert b.bpida_pdb_create(4, None, ctypes.byref(h), None) == bpida.EINVAL
+    assert b.bpida_pdb_create(4, (ctypes.c_int * 16)(*ok15), None, None) == bpida.EINVAL
+    cfg = bpida.make_config(4)
+    assert b.bpida_solve_pdb(ctypes.byref(cfg), None, None, 0, None, None, None, None, None, None,
+                             None) == bpida.EINVAL
+    assert b.bpida_pdb_groups(None) == 0
+    assert b.bpida_pdb_table_bytes(None, 0) == 0
+    assert b.bpida_pdb_max_value(None, 0) == -1
+    assert b.bpida_pdb_copy_table(None, 0, None, 0, None) == bpida.EINVAL
