@@ -442,6 +442,160 @@ def run_workloads(args):
                       "data": "synthetic", "results": out}), flush=True)
 
 
+# k_search<4,512,0,1> (the pattern-database search kernel of batched calls):
+# warp instructions issued per node expanded and DRAM bytes per launch, from
+# ncu over all its launches of two batched solves of the 100 boards
+# (profiles/k_search_pdb555_perms15_100_batched.txt); None where not measured.
+INSTR_PER_EXPANSION_PDB = {"555": 14.8, "663": None}
+TRAFFIC_PER_LAUNCH_PDB = {"555": 13.8e6, "663": None}
+
+
+def run_pdb(args):
+    """The pattern-database heuristic (the memory-intensive heuristic the
+    paper's Section 7 names as future work) on the 100-permutation workload:
+    the tables are built on the device, then the plain step (one call per
+    board) and the batched step (one call) are timed as in the default leg
+    (L2 flushed between steps, so every step starts with the tables out of
+    L2), every result checked against the stored oracle results under the
+    same heuristic. The oracle, with tables it builds itself, is timed on the
+    host cores over all 100 boards."""
+    import torch
+
+    from paper_1705_02843_gb300 import bpida
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    part = args.pdb
+    groups = I.PDB_PARTITIONS[part]
+    insts = I.perms15_100()
+    n = len(insts)
+    gold = load_golden("perms15_100_pdb" + part)
+    boards = torch.from_numpy(I.packed_array(insts).view(np.int64)).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    pdb = bpida.PatternDb(4, groups)
+    build_s = time.perf_counter() - t0
+    table_bytes = sum(pdb.table_bytes(g) for g in range(len(groups)))
+
+    if args.profile_pdb is not None:
+        # host-driven loop (ncu cannot see kernels inside graphs with
+        # conditional nodes); -1: the batched call
+        b = boards if args.profile_pdb < 0 else boards[args.profile_pdb:args.profile_pdb + 1]
+        cfg = bpida.make_config(4, driver=1)
+        for _ in range(2):
+            s = bpida.solve(b, 4, cfg, pdb=pdb)
+            torch.cuda.synchronize(dev)
+        print(json.dumps({"profile_pdb": args.profile_pdb, "partition": part, "status": s.status,
+                          "nodes": int(s.nodes.cpu().numpy().view(np.uint64).sum()),
+                          "stats": bpida.last_stats()}), flush=True)
+        return
+
+    cfg = bpida.make_config(4)
+
+    def check(sols):
+        tot = 0
+        for i, h in enumerate(sols):
+            g = gold[i]
+            if h["status"] != 0 or h["length"] != g["length"] or h["nodes"] != g["nodes"] or \
+                    h["solutions"] != g["solutions"] or "".join(map(str, h["moves"])) != g["moves"]:
+                raise RuntimeError("pattern databases %s: board %d differs from the oracle" % (part, i))
+            tot += sum(h["nodes"])
+        return tot
+
+    def plain_step():
+        return [bpida.solve(boards[i:i + 1], 4, cfg, pdb=pdb) for i in range(n)]
+
+    def batched_step():
+        return [bpida.solve(boards, 4, cfg, pdb=pdb)]
+
+    def hosts(sols):
+        return [h for s in sols for h in s.to_host()]
+
+    def timed(step, k, warm):
+        for _ in range(warm):
+            step()
+        torch.cuda.synchronize(dev)
+        ms, sols = [], None
+        for _ in range(k):
+            flush.fill_(1)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sols = step()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        return ms, sols
+
+    with ClockSampler(0) as clk:
+        ms_plain, psols = timed(plain_step, args.steps, args.warmup)
+        ms_batch, bsols = timed(batched_step, args.steps, args.warmup)
+    clocks = clk.summary()
+    exp = check(hosts(psols))
+    if check(hosts(bsols)) != exp:
+        raise RuntimeError("batched and plain expansions differ")
+    t_plain = sum(ms_plain) / 1e3 / len(ms_plain)
+    t_batch = sum(ms_batch) / 1e3 / len(ms_batch)
+
+    # the search kernel alone: the batched call through the host-driven
+    # loop, every k_search launch bracketed by CUDA events on its stream
+    bpida.set_timing(True)
+    flush.fill_(1)
+    torch.cuda.synchronize(dev)
+    s = bpida.solve(boards, 4, bpida.make_config(4, driver=1), pdb=pdb)
+    torch.cuda.synchronize(dev)
+    st = bpida.last_stats()
+    bpida.set_timing(False)
+    check(s.to_host())
+    kern_rate = st["search_nodes"] / (st["search_ms"] / 1e3)
+    roof = None
+    I_pdb = INSTR_PER_EXPANSION_PDB.get(part)
+    if I_pdb:
+        sm_mhz = clocks.get("sm_mhz") or 2070.0
+        peak = 152 * 4 * sm_mhz * 1e6
+        roof = {"kernel": "k_search<4,512,0,1>", "bound": "alu", "achieved": kern_rate * I_pdb, "peak": peak,
+                "unit": "warp-instructions/s", "frac": kern_rate * I_pdb / peak,
+                "traffic": TRAFFIC_PER_LAUNCH_PDB.get(part), "instr_per_expansion": I_pdb,
+                "note": "the integer ALU pipe (a warp instruction every 2 cycles per sub-partition) "
+                        "is 75 % busy in the ncu capture: the kernel is bound by it, not by issue"}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+
+        t0 = time.perf_counter()
+        opdb = oracle.PatternDb(4, groups)
+        ob = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        res = oracle.solve_batch(4, I.tiles_array(insts), pdb=opdb)
+        ot = time.perf_counter() - t0
+        onodes = sum(r.total_nodes for r in res)
+        cpu = {"value": onodes / ot, "unit": "expansions/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "all %d boards, %d expansions, %.1f s (tables built in %.1f s, not included)" % (
+                   n, onodes, ot, ob),
+               "instances_per_s": n / ot}
+    line = {
+        "metric": METRIC + " (pattern-database heuristic)",
+        "value": exp / t_plain, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_plain * 1e3, "higher_is_better": True, "dtype": "int64", "data": "synthetic",
+        "instances_per_s": n / t_plain,
+        "batched": {"value": exp / t_batch, "instances_per_s": n / t_batch, "ms_per_step": t_batch * 1e3},
+        "expansions_per_step": exp,
+        "search_kernel": {"expansions_per_s": kern_rate, "launches": st["passes"], "search_ms": st["search_ms"]},
+        "config": {"workload": "perms15_100 (100 seeded random solvable 15-puzzle boards), all-optimal-solutions "
+                               "mode, additive pattern databases, groups " + json.dumps(groups),
+                   "table_bytes": table_bytes, "device_build_s": build_s, "l2": "flushed between steps"},
+        "parity": {"checked": n, "mismatched": 0, "against": "tests/golden/perms15_100_pdb%s.json" % part},
+        "roofline": roof, "clocks": clocks, "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    pdb.close()
+
+
 def pick_cpu_sample(insts, gold, budget_nodes):
     cores = os.cpu_count() or 1
     if gold:
@@ -479,6 +633,10 @@ def main():
     ap.add_argument("--serving-max-requests", type=int, default=20000)
     ap.add_argument("--serving-slice-us", type=int, default=None,
                     help="time slice of a device step in microseconds (0 = none; default: the library's)")
+    ap.add_argument("--pdb", default=None, choices=sorted(I.PDB_PARTITIONS),
+                    help="time the pattern-database heuristic with this tile partition")
+    ap.add_argument("--profile-pdb", type=int, default=None, metavar="IDX",
+                    help="with --pdb: solve board IDX (-1: all, one call) twice through the host-driven loop")
     ap.add_argument("--driver", default="graph", choices=["graph", "host"],
                     help="graph: each solve call is one CUDA graph launch (default); host: the "
                          "host launches every kernel (same kernels; ncu can list them)")
@@ -508,6 +666,9 @@ def main():
         return
     if args.thread_parallel:
         run_thread_parallel(args)
+        return
+    if args.pdb:
+        run_pdb(args)
         return
     if args.workloads:
         run_workloads(args)

@@ -259,6 +259,15 @@ def serving_stream(rate_per_s: float, count: int, seed: int = 300000):
     return out
 
 
+# Tile groups of the pattern-database heuristic used by the benchmarks (a
+# configuration, not an algorithm: each group's table is built by the solver
+# or by the oracle). 5-5-5: three 16 MB tables (L2-resident); 6-6-3: two
+# 256 MB tables and a 64 KB one (beyond L2, read from HBM).
+PDB_PARTITIONS = {
+    "555": [[1, 2, 3, 4, 5], [6, 7, 8, 9, 10], [11, 12, 13, 14, 15]],
+    "663": [[1, 2, 3, 4, 5, 6], [7, 8, 9, 10, 11, 12], [13, 14, 15]],
+}
+
 WORKLOADS = {
     "walks15_16x40": walks15_16x40,
     "perms15_100": perms15_100,

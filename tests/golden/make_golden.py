@@ -7,7 +7,10 @@ arrive, so an interrupted run keeps what it finished; a rerun skips the
 instances already present.
 
 usage: python tests/golden/make_golden.py WORKLOAD [--threads N]
-       [--budget NODES] [--only-kind walk|perm]
+       [--budget NODES] [--only-kind walk|perm] [--pdb PARTITION]
+
+With --pdb the heuristic is the oracle's pattern databases for that tile
+partition (inputs.PDB_PARTITIONS) and the file is WORKLOAD_pdbPARTITION.json.
 """
 import argparse
 import json
@@ -31,10 +34,13 @@ def main():
     ap.add_argument("--budget", type=int, default=0, help="per-instance node budget (0 = none)")
     ap.add_argument("--only-kind", default=None)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--pdb", default=None, choices=sorted(I.PDB_PARTITIONS))
     args = ap.parse_args()
 
     insts = I.WORKLOADS[args.workload]()
-    path = args.out or os.path.join(os.path.dirname(os.path.abspath(__file__)), args.workload + ".json")
+    name = args.workload + ("_pdb" + args.pdb if args.pdb else "")
+    pdb = oracle.PatternDb(insts[0].W, I.PDB_PARTITIONS[args.pdb]) if args.pdb else None
+    path = args.out or os.path.join(os.path.dirname(os.path.abspath(__file__)), name + ".json")
     done = {}
     if os.path.exists(path):
         with open(path) as f:
@@ -49,6 +55,8 @@ def main():
             "workload": args.workload,
             "generator": "paper_1705_02843_gb300.inputs." + I.WORKLOADS[args.workload].__name__,
             "oracle": "oracle/ida_oracle.c (count-all mode)",
+            "heuristic": ("pattern databases, groups %s" % I.PDB_PARTITIONS[args.pdb]) if args.pdb
+                         else "Manhattan distance",
             "node_budget": args.budget,
             "instances": [done[k] for k in sorted(done)],
         }
@@ -60,7 +68,7 @@ def main():
     def work(i):
         x = insts[i]
         t0 = time.time()
-        r = oracle.solve(x.W, x.tiles, count_all=True, node_budget=args.budget)
+        r = oracle.solve(x.W, x.tiles, count_all=True, node_budget=args.budget, pdb=pdb)
         rec = {
             "index": i, "seed": x.seed, "kind": x.kind, "walk_len": x.walk_len,
             "status": r.status, "length": r.length, "h0": r.h0, "iters": r.iters,
