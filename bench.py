@@ -61,6 +61,13 @@ INSTR_PER_EXPANSION = 5.86
 INSTR_PER_EXPANSION_PLAIN_MIX = 7.65
 # DRAM bytes (read + write) per k_search launch over those launches.
 TRAFFIC_PER_LAUNCH = 1745542
+# Share of k_search's warp instructions that run on the integer ALU pipe
+# (16 lanes per scheduler: one warp instruction every 2 cycles), from ncu
+# over 80 launches of a batched solve
+# (profiles/k_search_15puzzle_batched_pipe_mix.txt). Above one half the ALU
+# pipe, not issue, bounds the kernel: its ceiling is the issue peak divided
+# by 2 x share.
+ALU_PIPE_SHARE = 0.537
 
 
 def golden_path(name):
@@ -446,8 +453,9 @@ def run_workloads(args):
 # warp instructions issued per node expanded and DRAM bytes per launch, from
 # ncu over all its launches of two batched solves of the 100 boards
 # (profiles/k_search_pdb555_perms15_100_batched.txt); None where not measured.
-INSTR_PER_EXPANSION_PDB = {"555": 14.8, "663": None}
-TRAFFIC_PER_LAUNCH_PDB = {"555": 13.8e6, "663": None}
+INSTR_PER_EXPANSION_PDB = {"555": 14.8, "663": 16.5}
+TRAFFIC_PER_LAUNCH_PDB = {"555": 13.8e6, "663": 62.5e6}
+ALU_PIPE_SHARE_PDB = {"555": 0.589, "663": 0.591}
 
 
 def run_pdb(args):
@@ -560,8 +568,8 @@ def run_pdb(args):
         roof = {"kernel": "k_search<4,512,0,1>", "bound": "alu", "achieved": kern_rate * I_pdb, "peak": peak,
                 "unit": "warp-instructions/s", "frac": kern_rate * I_pdb / peak,
                 "traffic": TRAFFIC_PER_LAUNCH_PDB.get(part), "instr_per_expansion": I_pdb,
-                "note": "the integer ALU pipe (a warp instruction every 2 cycles per sub-partition) "
-                        "is 75 % busy in the ncu capture: the kernel is bound by it, not by issue"}
+                "alu_pipe": {"share": ALU_PIPE_SHARE_PDB[part], "peak": peak / (2 * ALU_PIPE_SHARE_PDB[part]),
+                             "frac": kern_rate * I_pdb / (peak / (2 * ALU_PIPE_SHARE_PDB[part]))}}
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -644,6 +652,9 @@ def main():
                     help="solve board IDX alone, twice, through the host-driven loop with one "
                          "search pass per iteration (for ncu captures: the final iteration's "
                          "k_search launch is number iters-1), print its statistics and exit")
+    ap.add_argument("--profile-batched", action="store_true",
+                    help="solve all boards of the workload in one call, twice, through the host-driven loop "
+                         "(for ncu captures of the search kernel at full occupancy)")
     ap.add_argument("--profile-default", action="store_true",
                     help="with --profile-case: keep the default hand-back (as in the bench)")
     ap.add_argument("--profile-width", type=int, default=4, choices=[4, 5],
@@ -688,6 +699,15 @@ def main():
         pg = dist
 
     insts = I.WORKLOADS[args.workload]()
+    if args.profile_batched:
+        b = torch.from_numpy(I.packed_array(insts).view(np.int64)).to(dev)
+        for rep in range(2):
+            s = bpida.solve(b, 4, bpida.make_config(4, driver=1))
+            torch.cuda.synchronize(dev)
+        print(json.dumps({"profile_batched": len(insts), "status": s.status,
+                          "nodes": int(s.nodes.cpu().numpy().view(np.uint64).sum()),
+                          "stats": bpida.last_stats()}), flush=True)
+        return
     if args.profile_case is not None:
         W = args.profile_width
         # the 24-puzzle case: a walk of the 1024-walk workload, with the
@@ -880,7 +900,12 @@ def main():
                 "issue_utilization_plain_mix": s_nodes * INSTR_PER_EXPANSION_PLAIN_MIX / (s_ms / 1e3) / 1e9 / peak,
                 "expansions_per_s_in_kernel": s_nodes / (s_ms / 1e3),
                 "expansions_per_s_in_kernel_timed_steps": dev_nodes / (dev_ms / 1e3) if dev_ms else None,
-                "peak_basis": "%d SMs x 4 schedulers x %.0f MHz median SM clock sampled during the run" % (sms, f_mhz)}
+                "peak_basis": "%d SMs x 4 schedulers x %.0f MHz median SM clock sampled during the run" % (sms, f_mhz),
+                "alu_pipe": {"share": ALU_PIPE_SHARE, "peak": peak / (2 * ALU_PIPE_SHARE),
+                             "frac": achieved / (peak / (2 * ALU_PIPE_SHARE)),
+                             "basis": "the integer ALU pipe takes a warp instruction every 2 cycles per "
+                                      "scheduler; with this share of ALU instructions it caps issue at "
+                                      "1 / (2 x share) per cycle"}}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": peak, "unit": "Gwarp-inst/s", "frac": None,
                 "traffic": None, "kernel": "k_search<4,512,1>",
