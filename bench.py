@@ -449,13 +449,13 @@ def run_workloads(args):
                       "data": "synthetic", "results": out}), flush=True)
 
 
-# k_search<4,512,0,1> (the pattern-database search kernel of batched calls):
+# k_search<4,384,0,1> (the pattern-database search kernel of batched calls):
 # warp instructions issued per node expanded and DRAM bytes per launch, from
 # ncu over all its launches of two batched solves of the 100 boards
 # (profiles/k_search_pdb555_perms15_100_batched.txt); None where not measured.
-INSTR_PER_EXPANSION_PDB = {"555": 14.8, "663": 16.5}
-TRAFFIC_PER_LAUNCH_PDB = {"555": 13.8e6, "663": 62.5e6}
-ALU_PIPE_SHARE_PDB = {"555": 0.589, "663": 0.591}
+INSTR_PER_EXPANSION_PDB = {"555": 14.5, "663": None}
+TRAFFIC_PER_LAUNCH_PDB = {"555": 13.8e6, "663": None}
+ALU_PIPE_SHARE_PDB = {"555": 0.528, "663": None}
 
 
 def run_pdb(args):
@@ -565,11 +565,12 @@ def run_pdb(args):
     if I_pdb:
         sm_mhz = clocks.get("sm_mhz") or 2070.0
         peak = 152 * 4 * sm_mhz * 1e6
-        roof = {"kernel": "k_search<4,512,0,1>", "bound": "alu", "achieved": kern_rate * I_pdb, "peak": peak,
+        roof = {"kernel": "k_search<4,384,0,1>", "bound": "alu", "achieved": kern_rate * I_pdb, "peak": peak,
                 "unit": "warp-instructions/s", "frac": kern_rate * I_pdb / peak,
                 "traffic": TRAFFIC_PER_LAUNCH_PDB.get(part), "instr_per_expansion": I_pdb,
                 "alu_pipe": {"share": ALU_PIPE_SHARE_PDB[part], "peak": peak / (2 * ALU_PIPE_SHARE_PDB[part]),
-                             "frac": kern_rate * I_pdb / (peak / (2 * ALU_PIPE_SHARE_PDB[part]))}}
+                             "frac": kern_rate * I_pdb / (peak / (2 * ALU_PIPE_SHARE_PDB[part]))}
+                if ALU_PIPE_SHARE_PDB.get(part) else None}
 
     cpu = None
     if not args.no_cpu_baseline:

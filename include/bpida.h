@@ -328,7 +328,7 @@ bpida_status bpida_pdb_copy_table(const bpida_pdb *pdb, int group, uint8_t *dst,
 
 /* bpida_solve_ex with the pattern-database heuristic `pdb` (built on the
  * current device, for cfg->width; width 0 means the tables' width).
- * cfg->variant must be 0 and cfg->stack_entries 0, 384 or 512; everything
+ * cfg->variant must be 0 and cfg->stack_entries 0 (= 384), 384 or 512; everything
  * else (first-solution mode, node budgets, the graph and host drivers) is
  * as in bpida_solve_ex. Returns BPIDA_EINVAL for a null or foreign pdb. */
 bpida_status bpida_solve_pdb(const bpida_config *cfg, const bpida_pdb *pdb, const uint64_t *boards, int n,

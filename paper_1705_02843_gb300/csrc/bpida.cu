@@ -288,7 +288,8 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     g.fuse = fuse;
     const int wpb = cfg.variant == 1 ? 1 : cfg.wpb;  // the paper's kernel: block = warp
     g.threads = wpb * 32;
-    g.smem = SharedLut<W>::BYTES + (size_t)wpb * S * WarpStack<W>::ENTRY_BYTES;
+    // search stack entries: 16 bytes, 24 for W = 5 and the pattern-database search
+    g.smem = SharedLut<W>::BYTES + (size_t)wpb * S * WarpStack<W, (W == 5) || PDB>::ENTRY_BYTES;
     // one kernel serves every block size (and the serving path), so its
     // dynamic shared memory limit is set once to the device's maximum; the
     // blocks per SM are looked up once per (device, block size, kernel)
@@ -399,6 +400,7 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
         d.pdb.tab = cfg.pdb->tab;
         d.pdb.info = cfg.pdb->d_info;
         d.pdb.goal = cfg.pdb->goal;
+        d.pdb.goal_sb = cfg.pdb->goal_sb;
     }
 
     CallDesc desc;
@@ -514,8 +516,11 @@ bpida_status run_w(const Settings &cfg, const uint64_t *boards, int n, int *out_
                    uint64_t *out_nodes, int *out_iters, int *out_status, uint64_t *out_sol, cudaStream_t st)
 {
     if (cfg.pdb) {
-        // pattern databases: 8- and 15-puzzle, stacks of 384 or 512 entries
+        // pattern databases: 8- and 15-puzzle, stacks of 256, 384 or 512 entries
         if constexpr (W <= 4) {
+            if (cfg.S == 256)
+                return run<W, 256, true>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status,
+                                         out_sol, st);
             if (cfg.S == 384)
                 return run<W, 384, true>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status,
                                          out_sol, st);
@@ -661,8 +666,11 @@ bpida_status bpida_solve_pdb(const bpida_config *cfg_in, const bpida_pdb *pdb, c
         c.count_all = 1;
     if (c.width == 0)
         c.width = pdb->width;
-    if (c.stack_entries != 0 && c.stack_entries != 384 && c.stack_entries != 512)
+    if (c.stack_entries != 0 && c.stack_entries != 256 && c.stack_entries != 384 && c.stack_entries != 512)
         return BPIDA_EINVAL;
+    // 24-byte stack entries: 384 of them per warp keep six 4-warp blocks per SM
+    if (c.stack_entries == 0)
+        c.stack_entries = 384;
     Settings cfg;
     const bpida_status bad = parse_settings(&c, n, cfg);
     if (bad != BPIDA_OK)

@@ -297,21 +297,25 @@ struct Fuse {
 // the search's slack arithmetic (a child keeps slack s or drops to s - 2) is
 // the Manhattan one; only the direction of the step is read from a table.
 //
-// The search kernel works on the inverse board: 4-bit slot s holds the
-// position of the tile in slot s (slot 0: the blank; then the groups' tiles,
-// group by group, in increasing order), so a group's index is one field of
-// the inverse plus the blank's nibble. Stack entries stay 16 bytes: the
-// inverse takes the board's place and the metadata carries h_g mod 4 of
-// every group (enough to tell h_g + 1 from h_g - 1).
+// Tiles are renumbered into slots (slot 0: the blank; then the groups'
+// tiles, group by group, in increasing order). The search kernel's stack
+// entries (24 bytes) hold the slot board (4-bit field p: the slot of the
+// tile at cell p) and the inverse board (field s: the cell of the tile in
+// slot s), so the tile that moves is one field of the first, and a group's
+// index is one field of the second plus the blank's nibble; the metadata
+// carries h_g mod 4 of every group (enough to tell h_g + 1 from h_g - 1).
 static constexpr int PDB_MAX_GROUPS = 6;
 static constexpr int PDB_MAX_TILES = 6;    // per group: a table of 16^(k+1) bytes (256 MB at k = 6)
 static constexpr int PDB_VSHIFT = 20;      // stack metadata: h_g mod 4 at bits 20 + 2g
 static constexpr uint32_t PDB_VMASK = 0xFFF00000u;
+struct PdbSlot {
+    unsigned goff;  // bit offset of the slot's group field in the inverse board
+    unsigned mask;  // (1 << field width) - 1
+    unsigned vsh;   // metadata bit of h_g mod 4
+    unsigned base;  // byte offset of the group's table
+};
 struct PdbInfo {
-    // per slot s >= 1: bits 0..7 the group's field offset in the inverse,
-    // 8..15 its width, 16..23 the metadata bit of h_g mod 4, 32..63 the
-    // byte offset of the group's table (slot 0: zero)
-    unsigned long long slot[16];
+    PdbSlot slot[16];  // per slot s >= 1 (slot 0: zero)
     unsigned char slot_of_tile[16], tile_of_slot[16];
     int ng;
     int goff[PDB_MAX_GROUPS], gbits[PDB_MAX_GROUPS];
@@ -321,6 +325,7 @@ struct PdbDev {
     const unsigned char *tab;  // all groups' tables, one after another (null: Manhattan distance)
     const PdbInfo *info;       // device copy of the layout
     unsigned long long goal;   // the goal's inverse board
+    unsigned long long goal_sb;  // the goal's slot board
 };
 
 struct Tune {
@@ -458,6 +463,18 @@ template <int W> __device__ __forceinline__ uint64_t pdb_inverse(uint64_t b, con
         v |= (uint64_t)p << (4 * pi.slot_of_tile[tile_at<W>(b, p)]);
     return v;
 }
+// A search stack board: inverse board (high half) and slot board (low half).
+template <int W> __device__ __forceinline__ u128 pdb_encode(uint64_t b, const PdbInfo &pi)
+{
+    uint64_t inv = 0, sb = 0;
+#pragma unroll
+    for (int p = 0; p < Geo<W>::N; ++p) {
+        const uint64_t s = pi.slot_of_tile[tile_at<W>(b, p)];
+        inv |= (uint64_t)p << (4 * s);
+        sb |= s << (4 * p);
+    }
+    return ((u128)inv << 64) | sb;
+}
 // The position -> tile board of an inverse board.
 template <int W> __device__ __forceinline__ uint64_t pdb_board(uint64_t inv, const PdbInfo &pi)
 {
@@ -492,12 +509,12 @@ __device__ __forceinline__ bool pdb_away(const PdbDev &d, const PdbInfo &pi, uin
                                          unsigned tile)
 {
     const uint32_t j = pi.slot_of_tile[tile];
-    const unsigned long long inf = pi.slot[j];
-    const uint32_t goff = (uint32_t)inf & 255u, gbits = ((uint32_t)inf >> 8) & 255u;
+    const PdbSlot sl = pi.slot[j];
     const uint64_t dd = (uint64_t)(p ^ np);
     const uint64_t child = inv ^ (dd << (4 * j)) ^ dd;
-    const unsigned char *t = d.tab + (inf >> 32);
-    return t[pdb_index(child, goff, gbits)] > t[pdb_index(inv, goff, gbits)];
+    const unsigned char *t = d.tab + sl.base;
+    const uint32_t gbits = (uint32_t)__popc(sl.mask);
+    return t[pdb_index(child, sl.goff, gbits)] > t[pdb_index(inv, sl.goff, gbits)];
 }
 
 // ---- warp stack entries ----
@@ -520,9 +537,12 @@ template <int W> __device__ __forceinline__ uint32_t rec_from_sm(uint32_t m)
 }
 
 // W <= 4: one 16-byte entry {board lo, board hi, meta, origin}.
-// W == 5: a 16-byte board array and an 8-byte {meta, origin} array.
+// W == 5, and the pattern-database search: a 16-byte board array (the
+// 128-bit board; slot board and inverse board) and an 8-byte {meta, origin}
+// array.
 template <int W, bool Wide = (W == 5)> struct WarpStack;
 template <int W> struct WarpStack<W, false> {
+    typedef uint64_t Board;
     static constexpr int ENTRY_BYTES = 16;
     uint4 *e;
     __device__ __forceinline__ void init(unsigned char *base, int) { e = (uint4 *)base; }
@@ -539,6 +559,7 @@ template <int W> struct WarpStack<W, false> {
     }
 };
 template <int W> struct WarpStack<W, true> {
+    typedef u128 Board;
     static constexpr int ENTRY_BYTES = 24;
     uint4 *eb;
     uint2 *em;
@@ -640,8 +661,8 @@ template <int W> __device__ __forceinline__ LutRow<W> lut_row_sh(const unsigned 
 }
 
 // PDB: stack entries hold inverse boards; records hold boards.
-template <int W, int S, bool PDB = false>
-__device__ __forceinline__ void hand_back_stack(const Dev<W> &a, Rec<W> *out, const WarpStack<W> &stk,
+template <int W, int S, bool PDB = false, typename Stack = WarpStack<W>>
+__device__ __forceinline__ void hand_back_stack(const Dev<W> &a, Rec<W> *out, const Stack &stk,
                                                 int from, int k, unsigned inst, int lane,
                                                 const PdbInfo *pi = nullptr)
 {
@@ -657,12 +678,12 @@ __device__ __forceinline__ void hand_back_stack(const Dev<W> &a, Rec<W> *out, co
         return;
     }
     for (int j = lane; j < k; j += 32) {
-        typename Geo<W>::B b;
+        typename Stack::Board b;
         uint32_t m, o;
         stk.get(from + j, b, m, o);
         Rec<W> r;
         if constexpr (PDB)
-            r.b = pdb_board<W>(b, *pi);
+            r.b = pdb_board<W>((uint64_t)(b >> 64), *pi);
         else
             r.b = b;
         r.meta = rec_from_sm<W>(m);
@@ -726,12 +747,14 @@ __device__ __forceinline__ void hand_back_records(const Dev<W> &a, bool frontier
 
 template <int W> __device__ void end_of_pass(const Dev<W> &a);
 
-// The goal as the search kernel stores boards (PDB: the inverse board).
+// The search kernel's board type and its goal (PDB: inverse and slot
+// boards in one 128-bit value).
+template <int W, bool PDB> using SearchBoard = typename std::conditional<PDB, u128, typename Geo<W>::B>::type;
 template <int W, bool PDB>
-__device__ __forceinline__ typename Geo<W>::B search_goal(const Dev<W> &a)
+__device__ __forceinline__ SearchBoard<W, PDB> search_goal(const Dev<W> &a)
 {
     if constexpr (PDB)
-        return (typename Geo<W>::B)a.pdb.goal;
+        return ((u128)a.pdb.goal << 64) | a.pdb.goal_sb;
     else
         return goal_board<W>();
 }
@@ -751,6 +774,8 @@ template <int W, int S, bool FUSE = false, bool PDB = false>
 __global__ void k_search(const Dev<W> a)
 {
     typedef typename Geo<W>::B B;
+    typedef SearchBoard<W, PDB> SB;  // what a stack entry holds (B, or the PDB pair)
+    typedef WarpStack<W, (W == 5) || PDB> Stack;
     constexpr int BITS = Geo<W>::BITS;
     extern __shared__ __align__(16) unsigned char smem[];
     // end-of-pass bookkeeping is combined per block, so that the grid-wide
@@ -783,18 +808,18 @@ __global__ void k_search(const Dev<W> a)
     const bool first_only = a.desc->first_only != 0;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpStack<W> stk;
-    stk.init(smem + SharedLut<W>::BYTES + (size_t)warp * S * WarpStack<W>::ENTRY_BYTES, S);
+    Stack stk;
+    stk.init(smem + SharedLut<W>::BYTES + (size_t)warp * S * Stack::ENTRY_BYTES, S);
     // this warp's overflow stack in global memory: the oldest open nodes go
     // there when the shared stack is full and come back when it drains
     // (24-puzzle only: its deeper trees overflow the shared stack often)
     constexpr bool OVF = (W == 5);
-    WarpStack<W> ovf;
+    Stack ovf;
     const size_t gwarp = (size_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    ovf.init(a.ovf + gwarp * (size_t)a.ovf_cap * WarpStack<W>::ENTRY_BYTES, a.ovf_cap);
+    ovf.init(a.ovf + gwarp * (size_t)a.ovf_cap * Stack::ENTRY_BYTES, a.ovf_cap);
     int ovf_n = 0;
     const unsigned lt = (1u << lane) - 1u;
-    const B GOAL = search_goal<W, PDB>(a);
+    const SB GOAL = search_goal<W, PDB>(a);
     const int n_in = a.ctrl->n_in;
     const int total_warps = gridDim.x * (blockDim.x >> 5);
     const int chunk = max(1, min(32, n_in / (total_warps * 4)));
@@ -859,10 +884,10 @@ __global__ void k_search(const Dev<W> a)
             const bool dropped = watch && *(volatile unsigned *)&a.cnt.aborted[inst0];
             if (lane < cnt && !dropped) {
                 if constexpr (PDB) {
-                    const uint64_t inv = pdb_inverse<W>(r.b, *pi);
+                    const u128 e = pdb_encode<W>(r.b, *pi);
                     uint32_t vb;
-                    pdb_h(a.pdb, *pi, inv, &vb);
-                    stk.put(lane, inv, sm_from_rec<W>(r.meta) | vb, r.origin);
+                    pdb_h(a.pdb, *pi, (uint64_t)(e >> 64), &vb);
+                    stk.put(lane, e, sm_from_rec<W>(r.meta) | vb, r.origin);
                 } else {
                     stk.put(lane, r.b, sm_from_rec<W>(r.meta), r.origin);
                 }
@@ -882,7 +907,7 @@ __global__ void k_search(const Dev<W> a)
                     // refill from the overflow stack (its most recent spill)
                     const int k = min(ovf_n, S / 2);
                     for (int j = lane; j < k; j += 32) {
-                        B bb;
+                        SB bb;
                         uint32_t mm, oo;
                         ovf.get(ovf_n - k + j, bb, mm, oo);
                         stk.put(j, bb, mm, oo);
@@ -903,7 +928,7 @@ __global__ void k_search(const Dev<W> a)
                         atomicAdd(&a.ctrl->spills, 1ull);
                     if (OVF && ovf_n + k <= a.ovf_cap) {
                         for (int j = lane; j < k; j += 32) {
-                            B bb;
+                            SB bb;
                             uint32_t mm, oo;
                             stk.get(j, bb, mm, oo);
                             ovf.put(ovf_n + j, bb, mm, oo);
@@ -916,7 +941,7 @@ __global__ void k_search(const Dev<W> a)
                     for (int j0 = 0; j0 < top - k; j0 += 32) {
                         const int j = j0 + lane;
                         const bool ok = j < top - k;
-                        B bb = 0;
+                        SB bb = 0;
                         uint32_t mm = 0, oo = 0;
                         if (ok)
                             stk.get(k + j, bb, mm, oo);
@@ -928,7 +953,7 @@ __global__ void k_search(const Dev<W> a)
                     top -= k;
                 }
                 const bool act = lane < n;
-                B b = 0;
+                SB b = 0;
                 uint32_t mt = 0, org = 0;
                 if (act)
                     stk.get(top - n + lane, b, mt, org);
@@ -971,8 +996,10 @@ __global__ void k_search(const Dev<W> a)
                 bool pruned = false;
                 int base = top;
                 if constexpr (PDB) {
-                    // b is the inverse board; the step's direction comes from
-                    // the moved tile's group table, h_g mod 4 from the metadata
+                    // b holds the inverse board (high half) and the slot board
+                    // (low half); the step's direction comes from the moved
+                    // tile's group table, h_g mod 4 from the metadata
+                    const uint64_t sb = (uint64_t)b, inv = (uint64_t)(b >> 64);
                     const uint32_t vkeep = mt & PDB_VMASK;
                     bool bad = false;
 #pragma unroll
@@ -980,24 +1007,24 @@ __global__ void k_search(const Dev<W> a)
                         const bool legal = (allowed >> m) & 1u;
                         const uint32_t sh_np = sh_p + (uint32_t)(4 * move_off<W>(m));
                         const uint32_t np = sh_np >> 2;
-                        // slot of the tile at np: the inverse's nibble equal to
-                        // np (bit 3 of each zero nibble of b ^ np...np; slot 0
-                        // holds the blank, which is not at np)
-                        const uint32_t rep = np * 0x11111111u;
-                        const uint32_t xl = (uint32_t)b ^ rep, xh = (uint32_t)(b >> 32) ^ rep;
-                        const uint32_t zl = ~(((xl & 0x77777777u) + 0x77777777u) | xl | 0x77777777u);
-                        const uint32_t zh = ~(((xh & 0x77777777u) + 0x77777777u) | xh | 0x77777777u);
-                        const uint32_t j4 = zl ? (uint32_t)__ffs((int)zl) - 4u : (uint32_t)__ffs((int)zh) + 28u;
-                        const unsigned long long inf = pi->slot[(j4 >> 2) & 15u];
+                        // slot of the tile that slides into the blank (an off-board
+                        // offset reads slot 0, whose entry is zero)
+                        const uint32_t j = BoardOps<W>::tile(sb, sh_np);
+                        const PdbSlot sl = pi->slot[j];
                         // the tile moves np -> p, the blank p -> np
                         const uint64_t dd = (uint64_t)((sh_p ^ sh_np) >> 2);
-                        const B child = b ^ (dd << j4) ^ dd;
-                        const uint32_t vsh = ((uint32_t)inf >> 16) & 255u;
+                        const uint64_t cinv = inv ^ (dd << (4 * j)) ^ dd;
+                        const uint32_t sh_q = (m < 2) ? sh_np : sh_p;  // lower of the two fields
+                        const uint64_t csb = BoardOps<W>::flip(sb, j * move_mul<W>(m), sh_q);
                         uint32_t v = 0;
-                        if (legal)
-                            v = __ldg(a.pdb.tab + (inf >> 32) +
-                                      pdb_index(child, (uint32_t)inf & 255u, ((uint32_t)inf >> 8) & 255u));
-                        const uint32_t vold = mt >> vsh;
+                        if (legal) {
+                            uint64_t f;
+                            asm("shr.b64 %0, %1, %2;" : "=l"(f) : "l"(cinv), "r"(sl.goff));
+                            // field | np << width, as one multiply-add (the field is below mask + 1)
+                            const uint32_t idx = ((uint32_t)f & sl.mask) + np * (sl.mask + 1u);
+                            v = __ldg(a.pdb.tab + sl.base + idx);
+                        }
+                        const uint32_t vold = mt >> sl.vsh;
                         // h_g rose by 1 (dv = 1) or fell by 1 (dv = 3); any other
                         // dv is an inconsistent table: it counts as a rise (so a
                         // subtree stays finite) and fails the call
@@ -1007,10 +1034,10 @@ __global__ void k_search(const Dev<W> a)
                         const bool push = legal && !(away && low);
                         pruned |= legal && away && low;
                         const uint32_t cm = ((sh_np + sbase + ((1u << (3 - m)) << 7)) - (away ? (2u << 11) : 0u)) |
-                                            (vkeep ^ (((v ^ vold) & 3u) << vsh));
+                                            (vkeep ^ (((v ^ vold) & 3u) << sl.vsh));
                         const unsigned pm = __ballot_sync(FULL, push);
                         if (push)
-                            stk.put(base + __popc(pm & lt), child, cm, org);
+                            stk.put(base + __popc(pm & lt), ((u128)cinv << 64) | csb, cm, org);
                         base += __popc(pm);
                     }
                     if (__any_sync(FULL, bad) && lane == 0)

@@ -189,9 +189,13 @@ bpida_status bpida_pdb_create(int width, const int *group_of_tile, bpida_pdb **o
             const int t = tiles[g][j];
             P.info.slot_of_tile[t] = (unsigned char)slot;
             P.info.tile_of_slot[slot] = (unsigned char)t;
-            P.info.slot[slot] = (unsigned long long)P.info.goff[g] | ((unsigned long long)P.info.gbits[g] << 8) |
-                                ((unsigned long long)(PDB_VSHIFT + 2 * g) << 16) | (base << 32);
-            P.goal |= (unsigned long long)t << (4 * slot);  // tile t's goal cell is t
+            P.info.slot[slot].goff = (unsigned)P.info.goff[g];
+            P.info.slot[slot].mask = (1u << P.info.gbits[g]) - 1u;
+            P.info.slot[slot].vsh = (unsigned)(PDB_VSHIFT + 2 * g);
+            P.info.slot[slot].base = (unsigned)base;
+            // tile t's goal cell is t: inverse field `slot` = t, slot-board field t = slot
+            P.goal |= (unsigned long long)t << (4 * slot);
+            P.goal_sb |= (unsigned long long)slot << (4 * t);
         }
         base += P.table_bytes[g];
     }

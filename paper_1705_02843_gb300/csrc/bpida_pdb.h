@@ -16,4 +16,5 @@ struct bpida_pdb {
     bp::PdbInfo info = {};                    // layout (host copy)
     bp::PdbInfo *d_info = nullptr;            // layout (device copy)
     unsigned long long goal = 0;              // the goal's inverse board
+    unsigned long long goal_sb = 0;           // the goal's slot board
 };

@@ -117,7 +117,7 @@ def perms_cheap(pdb555):
     return [w[i].tiles for i in order], [res[i] for i in order]
 
 
-@pytest.mark.parametrize("cfg", [dict(), dict(driver=1), dict(stack_entries=384),
+@pytest.mark.parametrize("cfg", [dict(), dict(driver=1), dict(stack_entries=256), dict(stack_entries=512),
                                  dict(split_target=1, min_pass_us=-1, exit_fraction_pct=1, min_rounds=32),
                                  dict(warps_per_block=8)])
 def test_perms_batched(pdb555, perms_cheap, cfg):
@@ -201,5 +201,5 @@ def test_empty_call_and_bad_arguments(pdb555, pdb8):
     one = torch.zeros(1, dtype=torch.int64, device="cuda:0")
     assert bpida.solve(one, 3, bpida.make_config(3), pdb=pdb).status == bpida.EINVAL   # width mismatch
     assert bpida.solve(one, 4, bpida.make_config(4, variant=1), pdb=pdb).status == bpida.EINVAL
-    assert bpida.solve(one, 4, bpida.make_config(4, stack_entries=256), pdb=pdb).status == bpida.EINVAL
+    assert bpida.solve(one, 4, bpida.make_config(4, stack_entries=768), pdb=pdb).status == bpida.EINVAL
     assert bpida.solve(one, 4, bpida.make_config(4), pdb=pdb8[1]).status == bpida.EINVAL
