@@ -453,9 +453,9 @@ def run_workloads(args):
 # warp instructions issued per node expanded and DRAM bytes per launch, from
 # ncu over all its launches of two batched solves of the 100 boards
 # (profiles/k_search_pdb555_perms15_100_batched.txt); None where not measured.
-INSTR_PER_EXPANSION_PDB = {"555": 14.5, "663": None}
-TRAFFIC_PER_LAUNCH_PDB = {"555": 13.8e6, "663": None}
-ALU_PIPE_SHARE_PDB = {"555": 0.528, "663": None}
+INSTR_PER_EXPANSION_PDB = {"555": 14.5, "663": 16.2}
+TRAFFIC_PER_LAUNCH_PDB = {"555": 13.8e6, "663": 62.2e6}
+ALU_PIPE_SHARE_PDB = {"555": 0.528, "663": 0.527}
 
 
 def run_pdb(args):
