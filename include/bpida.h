@@ -316,6 +316,9 @@ typedef struct bpida_pdb bpida_pdb;
  * owns the tables until bpida_pdb_destroy. Errors: BPIDA_EINVAL (bad
  * width or grouping), BPIDA_ENOMEM, BPIDA_ECUDA. */
 bpida_status bpida_pdb_create(int width, const int *group_of_tile, bpida_pdb **out, void *stream);
+/* Frees the tables (on the device they were built on). Solve calls return
+ * after their results are written, so this is safe once no other host
+ * thread is inside a call that uses `pdb`. */
 void bpida_pdb_destroy(bpida_pdb *pdb);
 int bpida_pdb_groups(const bpida_pdb *pdb);
 /* Bytes of group `group`'s table (0 for a bad group) and its largest entry
