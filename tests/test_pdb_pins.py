@@ -76,6 +76,25 @@ def test_tables_equal_independent_01bfs(W, groups):
     assert pdb.max_values == [max(P.pattern_distances(W, g).values()) for g in groups]
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_random_8puzzle_partitions_equal_independent_01bfs(seed):
+    """Seeded random partitions of the 8 tiles into groups of 1 to 4 tiles."""
+    rng = random.Random(seed)
+    tiles = list(range(1, 9))
+    rng.shuffle(tiles)
+    groups = []
+    while tiles:
+        k = rng.randint(1, min(4, len(tiles)))
+        groups.append(sorted(tiles[:k]))
+        tiles = tiles[k:]
+    pdb = oracle.PatternDb(3, groups)
+    for g, tab in zip(groups, pdb.tables):
+        ref = P.pattern_distances(3, g)
+        assert int((tab != 255).sum()) == len(ref) == math.perm(9, len(g) + 1)
+        idx = np.array([_index(pos, b) for pos, b in ref], dtype=np.int64)
+        assert np.array_equal(tab[idx], np.array(list(ref.values()), dtype=np.uint8)), groups
+
+
 def test_singleton_groups_reduce_to_manhattan(bfs):
     dist, count, order = bfs
     pdb = oracle.PatternDb(3, [[t] for t in range(1, 9)])
@@ -196,7 +215,13 @@ def test_555_partition_properties(pdb555, walks16):
     hb = pdb555.h_batch(np.array(boards, dtype=np.uint8))
     hn = pdb555.h_batch(np.array(nexts, dtype=np.uint8))
     assert set((hn - hb).tolist()) == {-1, 1}
-    assert all(int(v) >= P.manhattan_py(4, s) for s, v in zip(boards, hb))
+    mh = np.array([P.manhattan_py(4, s) for s in boards])
+    assert (hb >= mh).all() and ((hb - mh) % 2 == 0).all()
+    # random permutations of the goal's parity class as well as walks
+    perms = [x.tiles for x in I.perms15_100()[:50]]
+    hp = pdb555.h_batch(np.array(perms, dtype=np.uint8))
+    mp = np.array([P.manhattan_py(4, s) for s in perms])
+    assert (hp >= mp).all() and ((hp - mp) % 2 == 0).all()
     res = oracle.solve_batch(4, I.tiles_array(w), count_all=True, pdb=pdb555)
     for x, r, m in zip(w, res, md):
         assert r.status == oracle.OK
