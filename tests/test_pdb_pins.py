@@ -238,3 +238,28 @@ def test_bad_groups_are_rejected():
         oracle.PatternDb(3, [[1, 2, 3, 4], [4, 5, 6, 7, 8]])  # tile 4 twice
     with pytest.raises(ValueError):
         oracle.PatternDb(3, [[1, 2, 3, 4, 5, 6, 7], [8]])  # more than 6 tiles
+
+
+def test_blank_free_tables_would_be_inconsistent(bfs):
+    """Why the blank's cell is part of every abstract state: tables that keep
+    only the minimum over blank cells are still admissible but change h by up
+    to 7 along an 8-puzzle edge (G's tiles can wall the blank in), so the
+    search's slack arithmetic (s or s - 2) would not hold."""
+    import collections
+
+    dist, count, order = bfs
+    tabs = []
+    for g in G8:
+        m = collections.defaultdict(lambda: 1 << 30)
+        for (pos, b), v in P.pattern_distances(3, g).items():
+            m[pos] = min(m[pos], v)
+        tabs.append(m)
+
+    def h(s):
+        where = {v: p for p, v in enumerate(s)}
+        return sum(t[tuple(where[x] for x in sorted(g))] for g, t in zip(G8, tabs))
+
+    H = {s: h(s) for s in order}
+    steps = {H[n] - H[s] for s in order for _, n in P.neighbours(3, s)}
+    assert all(H[s] <= dist[s] for s in order)
+    assert max(steps) == 7 and min(steps) == -7
