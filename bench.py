@@ -478,6 +478,9 @@ def run_pdb(args):
     insts = I.perms15_100()
     n = len(insts)
     gold = load_golden("perms15_100_pdb" + part)
+    if gold is None:
+        raise RuntimeError("no stored oracle results for partition %s: run "
+                           "python tests/golden/make_golden.py perms15_100 --pdb %s" % (part, part))
     boards = torch.from_numpy(I.packed_array(insts).view(np.int64)).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
