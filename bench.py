@@ -552,6 +552,34 @@ def run_pdb(args):
     t_plain = sum(ms_plain) / 1e3 / len(ms_plain)
     t_batch = sum(ms_batch) / 1e3 / len(ms_batch)
 
+    # end to end through host buffers: pinned boards copied to the device and
+    # every result copied back inside the timed region (plain step)
+    packed = I.packed_array(insts)
+    host_boards = torch.from_numpy(packed.view(np.int64)).pin_memory()
+    ml, mi = bpida.max_len(4), bpida.max_iters(4)
+    host_out = {k: torch.empty(sz, dtype=dt).pin_memory() for k, sz, dt in (
+        ("len", n, torch.int32), ("moves", n * ml, torch.uint8), ("nodes", n * mi, torch.int64),
+        ("iters", n, torch.int32), ("status", n, torch.int32), ("solutions", n, torch.int64))}
+
+    def e2e_step():
+        dboards = host_boards.to(dev, non_blocking=True)
+        sols = [bpida.solve(dboards[i:i + 1], 4, cfg, pdb=pdb) for i in range(n)]
+        host_out["len"].copy_(torch.cat([x.length for x in sols]), non_blocking=True)
+        host_out["moves"].copy_(torch.cat([x.moves.reshape(-1) for x in sols]), non_blocking=True)
+        host_out["nodes"].copy_(torch.cat([x.nodes.reshape(-1) for x in sols]), non_blocking=True)
+        host_out["iters"].copy_(torch.cat([x.iters for x in sols]), non_blocking=True)
+        host_out["status"].copy_(torch.cat([x.inst_status for x in sols]), non_blocking=True)
+        host_out["solutions"].copy_(torch.cat([x.solutions for x in sols]), non_blocking=True)
+        return sols
+
+    ms_e2e, _ = timed(e2e_step, args.steps, 1)
+    if int(host_out["nodes"].numpy().view(np.uint64).sum()) != exp:
+        raise RuntimeError("end-to-end expansions differ")
+    t_e2e = sum(ms_e2e) / 1e3 / len(ms_e2e)
+    e2e = {"value": exp / t_e2e, "unit": UNIT, "instances_per_s": n / t_e2e,
+           "h2d_bytes_per_step": host_boards.numel() * 8,
+           "d2h_bytes_per_step": sum(t.numel() * t.element_size() for t in host_out.values())}
+
     # the search kernel alone: the batched call through the host-driven
     # loop, every k_search launch bracketed by CUDA events on its stream
     bpida.set_timing(True)
@@ -602,7 +630,7 @@ def run_pdb(args):
                                "mode, additive pattern databases, groups " + json.dumps(groups),
                    "table_bytes": table_bytes, "device_build_s": build_s, "l2": "flushed between steps"},
         "parity": {"checked": n, "mismatched": 0, "against": "tests/golden/perms15_100_pdb%s.json" % part},
-        "roofline": roof, "clocks": clocks, "cpu_baseline": cpu,
+        "e2e": e2e, "roofline": roof, "clocks": clocks, "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
     pdb.close()
