@@ -60,7 +60,10 @@ def h8(bfs, pdb8):
     return {s: int(v) for s, v in zip(order, h)}
 
 
-@pytest.mark.parametrize("W,groups", [(3, G8), (3, G8B), (4, G15_3)])
+@pytest.mark.parametrize("W,groups", [(3, G8), (3, G8B), (4, G15_3),
+                                      # 5- and 6-tile groups: the 24- and 28-bit indices of the
+                                      # 15-puzzle partitions used by the benchmarks
+                                      (3, [[1, 2, 3, 4, 5], [6, 7, 8]]), (3, [[2, 3, 5, 6, 7, 8], [1, 4]])])
 def test_tables_equal_independent_01bfs(W, groups):
     pdb = oracle.PatternDb(W, groups)
     N = W * W
