@@ -286,6 +286,15 @@ void bpida_server_destroy(bpida_server *sv);
 void bpida_set_timing(int on);
 void bpida_get_stats(bpida_stats *out);
 
+/* Fused iterations (calls of at most 8 boards in all-solutions mode without
+ * a node budget search several consecutive thresholds in one step): a step
+ * fuses the next thresholds while the highest of them is predicted (x8 per
+ * threshold) to expand at most `nodes` nodes, divided among the call's
+ * active boards. Results do not depend on it; only the number of steps and
+ * the nodes searched above a board's optimum do. 0 restores the default
+ * (8e6). Process-wide; takes effect at the next call. */
+void bpida_set_fuse_nodes(uint64_t nodes);
+
 /* Free the calling device's workspace. */
 void bpida_release_workspace(void);
 

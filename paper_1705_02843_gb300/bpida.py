@@ -22,6 +22,7 @@ BLOCK_PARALLEL, PAPER_KERNEL, PSIMPLE, PSTATICLB, PFULLLB = range(5)
 
 EXPORTS = (
     "bpida_max_len", "bpida_max_iters", "bpida_solve", "bpida_solve_ex", "bpida_set_timing",
+    "bpida_set_fuse_nodes",
     "bpida_get_stats", "bpida_release_workspace", "bpida_status_str", "bpida_solve_noalloc",
     "bpida_server_create", "bpida_server_submit", "bpida_server_poll", "bpida_server_in_flight",
     "bpida_server_get_stats", "bpida_server_clock", "bpida_server_set_time_slice", "bpida_server_destroy",
@@ -137,6 +138,8 @@ def load():
         lib.bpida_solve_ex.restype = ctypes.c_int
         lib.bpida_set_timing.argtypes = [ctypes.c_int]
         lib.bpida_set_timing.restype = None
+        lib.bpida_set_fuse_nodes.argtypes = [ctypes.c_uint64]
+        lib.bpida_set_fuse_nodes.restype = None
         lib.bpida_get_stats.argtypes = [ctypes.POINTER(Stats)]
         lib.bpida_get_stats.restype = None
         lib.bpida_release_workspace.argtypes = []
@@ -193,6 +196,11 @@ def status_str(code: int) -> str:
 
 def set_timing(on: bool) -> None:
     load().bpida_set_timing(1 if on else 0)
+
+
+def set_fuse_nodes(nodes: int) -> None:
+    """Node cap of a fused step's top threshold (0: the defaults); see bpida.h."""
+    load().bpida_set_fuse_nodes(int(nodes))
 
 
 def last_stats() -> dict:

@@ -24,6 +24,7 @@
 #include "bpida_thread.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -38,6 +39,7 @@ namespace {
 
 thread_local bpida_stats g_stats;
 thread_local int g_timing = 0;
+std::atomic<unsigned long long> g_fuse_nodes{0};  // 0: the defaults below
 std::mutex g_mu;
 
 struct DevBuf {
@@ -46,8 +48,9 @@ struct DevBuf {
 };
 
 // W, S, warps per block, n, frontier cap, hand-back percentage, min rounds, min pass time, variant,
-// fused iterations, pattern databases (their id; 0 = Manhattan distance)
-typedef std::tuple<int, int, int, int, int, int, int, int, int, int, unsigned long long> PlanKey;
+// fused iterations, pattern databases (their id; 0 = Manhattan distance), fused-step node cap
+typedef std::tuple<int, int, int, int, int, int, int, int, int, int, unsigned long long, unsigned long long>
+    PlanKey;
 
 struct Plan {
     cudaGraph_t graph = nullptr;
@@ -159,6 +162,9 @@ struct Settings {
 // share one step instead of one each. Calls with at most FUSE_MAX_N boards
 // use it (their steps are few and short, so the steps saved pay); larger
 // batches run the kernel without the fused counts.
+// (One value for both heuristics: with pattern databases h(start) lies closer
+// to the optimum, so a fused step searches thresholds above the solution
+// more often, but smaller caps cost more in extra steps than they save.)
 constexpr unsigned long long FUSE_NODES = 8000000ull;
 constexpr int FUSE_MAX_N = 8;
 
@@ -370,7 +376,8 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
         d.fuse.origin = (unsigned *)p;
         p += sizeof(unsigned) * FUSE_K * n;
         d.fuse.jump = (int *)p;
-        d.fuse.max_nodes = FUSE_NODES;
+        const unsigned long long set = g_fuse_nodes.load();
+        d.fuse.max_nodes = set ? set : FUSE_NODES;
     }
     {
         char *p = (char *)ws.ctr.p;
@@ -428,7 +435,7 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     const dim3 g_inst((n + 127) / 128);
     if (cfg.driver == 0) {
         const PlanKey key(W, S, cfg.wpb, n, g.tcap, cfg.exit_pct, cfg.min_rounds, cfg.min_pass_ns, cfg.variant,
-                          fuse ? 1 : 0, PDB ? cfg.pdb->id : 0ull);
+                          fuse ? 1 : 0, PDB ? cfg.pdb->id : 0ull, fuse ? d.fuse.max_nodes : 0ull);
         auto found = ws.plans.find(key);
         if (found == ws.plans.end() || !found->second.exec || found->second.gen != ws.gen) {
             ws.trim_plans();
@@ -700,6 +707,8 @@ bpida_status bpida_solve(const uint64_t *boards, int n, int *out_len, uint8_t *o
 }
 
 void bpida_set_timing(int on) { g_timing = on ? 1 : 0; }
+
+void bpida_set_fuse_nodes(uint64_t nodes) { g_fuse_nodes.store(nodes); }
 
 void bpida_get_stats(bpida_stats *out)
 {

@@ -393,3 +393,20 @@ def test_first_solution_mode_one_board_per_call():
         assert g["nodes"][:-1] == r.nodes[:-1]
         assert 1 <= g["nodes"][-1] <= r.nodes[-1]
         assert P.replay(4, t, g["moves"]) == list(range(16))
+
+
+@pytest.mark.parametrize("cap", [30000, 32000000])
+def test_fused_step_cap_does_not_change_results(cap):
+    """bpida_set_fuse_nodes only moves thresholds between steps: one-board
+    calls (fused) give the oracle's results at a small and a large cap."""
+    insts = I.walks15_16x40()[:6] + I.perms15_100()[:2]
+    tiles = [x.tiles for x in insts]
+    ref = oracle.solve_batch(4, np.array(tiles, dtype=np.uint8))
+    bpida.set_fuse_nodes(cap)
+    try:
+        for t, r in zip(tiles, ref):
+            rc, got = gpu_solve(4, [t])
+            assert rc == bpida.OK
+            check_against(4, [t], got, [r])
+    finally:
+        bpida.set_fuse_nodes(0)
