@@ -54,3 +54,40 @@ def test_permutations_in_goal_class_8puzzle():
     rng = I.Xoshiro256ss(11)
     for _ in range(200):
         assert tuple(I.random_permutation(3, rng)) in dist
+
+
+def test_pattern_database_partitions_are_well_formed():
+    for name, groups in I.PDB_PARTITIONS.items():
+        tiles = sorted(t for g in groups for t in g)
+        assert tiles == list(range(1, 16)), name
+        assert 1 <= len(groups) <= 6 and all(1 <= len(g) <= 6 for g in groups), name
+
+
+def test_stored_pattern_database_results_match_the_oracle():
+    """The stored oracle results the --pdb bench checks against: the ten
+    cheapest boards of the 5-5-5 file re-solved by the oracle now, and the
+    6-6-3 file's lengths and first solutions equal the Manhattan file's (any
+    admissible heuristic returns the same length, solution count and first
+    optimal path)."""
+    import json
+    import os
+
+    import oracle
+
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    md = {r["index"]: r for r in json.load(open(os.path.join(here, "perms15_100.json")))["instances"]}
+    insts = I.perms15_100()
+    for part in ("555", "663"):
+        doc = json.load(open(os.path.join(here, "perms15_100_pdb%s.json" % part)))
+        recs = {r["index"]: r for r in doc["instances"]}
+        assert sorted(recs) == list(range(100))
+        for i, r in recs.items():
+            assert r["status"] == 0 and r["seed"] == insts[i].seed
+            assert (r["length"], r["moves"], r["solutions"]) == (md[i]["length"], md[i]["moves"], md[i]["solutions"])
+            assert sum(r["nodes"]) < sum(md[i]["nodes"])
+    pdb = oracle.PatternDb(4, I.PDB_PARTITIONS["555"])
+    recs = json.load(open(os.path.join(here, "perms15_100_pdb555.json")))["instances"]
+    cheap = sorted(recs, key=lambda r: sum(r["nodes"]))[:10]
+    res = oracle.solve_batch(4, np.array([insts[r["index"]].tiles for r in cheap], dtype=np.uint8), pdb=pdb)
+    for r, o in zip(cheap, res):
+        assert o.nodes == r["nodes"] and o.limits == r["limits"] and o.h0 == r["h0"]
