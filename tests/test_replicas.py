@@ -49,3 +49,21 @@ def test_single_process_is_identity():
 
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.replica_throughput(100, 2.0, 1) == 50.0
+
+
+def test_bench_pattern_database_constants_cover_every_partition():
+    """Every tile partition the --pdb leg accepts has its measured kernel
+    figures, and the command line offers exactly those partitions."""
+    import subprocess
+    import sys
+
+    import bench
+    from paper_1705_02843_gb300 import inputs as I
+
+    parts = set(I.PDB_PARTITIONS)
+    for table in (bench.INSTR_PER_EXPANSION_PDB, bench.TRAFFIC_PER_LAUNCH_PDB, bench.ALU_PIPE_SHARE_PDB):
+        assert set(table) == parts
+        assert all(v is not None and v > 0 for v in table.values())
+    assert 0.5 < bench.ALU_PIPE_SHARE < 1.0
+    out = subprocess.run([sys.executable, bench.__file__, "--help"], capture_output=True, text=True, check=True).stdout
+    assert "--pdb {%s}" % ",".join(sorted(parts)) in out
