@@ -1,24 +1,30 @@
 #!/usr/bin/env python3
 """Benchmark of the GB300 Block-Parallel IDA* solver.
 
-Metric: 15-puzzle node expansions/s (and instances/s), plain vs batched,
+Metric: 15-puzzle node expansions/s (and instances/s), batched vs plain,
 with every integer result equal to the CPU oracle's.
 
-Workload (default): 100 seeded uniformly random solvable 15-puzzle boards
-(``inputs.perms15_100``; a stand-in for the paper's 100-instance benchmark
-set), Manhattan heuristic, all-optimal-solutions mode (the final iteration
-is searched to completion, so node counts are order-free). One step solves
-all 100 boards:
+Workload (default, the headline line): ``mixed15_4096``, 4096 seeded
+15-puzzle boards of mixed difficulty (every 20th a uniformly random solvable
+permutation, the rest random walks of 20-90 moves), Manhattan heuristic,
+all-optimal-solutions mode (the final iteration is searched to completion,
+so node counts are order-free). One step solves all 4096 boards:
 
-* plain (headline ``value``): one solve call per board, as in the paper's
-  one-instance-per-run experiments;
-* batched (``batched``): all 100 boards in one solve call.
+* batched (headline ``value``): all boards in one solve call (persistent
+  search warps shared by every board, per-board limits, the threshold loop
+  as one CUDA graph);
+* plain (``plain``): one solve call per board, as in the paper's
+  one-instance-per-run experiments, timed over fewer steps.
 
 Expansions are the nodes expanded over all iterations of all instances.
 Inputs are resident in HBM when a timed step starts; L2 is flushed (a
-256 MiB write) between steps. ``e2e`` repeats the plain step through the
-host-buffer path: pinned boards copied to the device and every result copied
-back inside the timed region.
+256 MiB write) between steps. ``e2e`` repeats the batched step from pinned
+host boards, copying the boards in and every result back inside the timed
+region. Sub-keys measure the other workloads: ``perms15_100`` (100 random
+permutations, plain and batched), ``walks24_1024`` (24-puzzle walks with a
+node budget), ``serving`` (the continuous-batching service under Poisson
+arrivals) and ``first_solution`` (first-solution mode against the oracle's
+first-solution mode on one host core, the paper's headline comparison).
 
 Multi-GPU: instances are independent, so each rank solves its own copy of
 the workload with no collective on the data path (replicas; weak scaling).
@@ -46,28 +52,33 @@ from paper_1705_02843_gb300 import inputs as I  # noqa: E402
 
 METRIC = "15-puzzle node expansions/s & instances/s, batched vs plain, oracle-exact"
 UNIT = "expansions/s"
-WORKLOAD_DESC = ("perms15_100: 100 seeded uniformly random solvable 15-puzzle boards "
-                 "(seeds 1001-1100), Manhattan distance, all-optimal-solutions mode")
+WORKLOAD_DESC = {
+    "mixed15_4096": "mixed15_4096: 4096 seeded 15-puzzle boards (seeds 100000-104095; every 20th a random "
+                    "solvable permutation, 205 in all; the rest random walks of 20-90 moves), Manhattan "
+                    "distance, all-optimal-solutions mode",
+    "perms15_100": "perms15_100: 100 seeded uniformly random solvable 15-puzzle boards (seeds 1001-1100), "
+                   "Manhattan distance, all-optimal-solutions mode",
+}
 
-# The plain form (one board per call) runs the search kernel's fused-iteration
-# variant k_search<4,512,1>. Warp instructions it issues per node expanded in
-# steady state (the work the method needs per expansion), from ncu
-# (smsp__inst_executed.sum / nodes) on the final iteration of board 0 run as
-# one pass: profiles/k_search_15puzzle_perms15_board0_final_iteration.txt.
-INSTR_PER_EXPANSION = 5.86
-# The same ratio over every k_search launch of a plain solve of board 0
-# (hand-back on, as in the benchmark): ramp-up, short passes and hand-back
-# copies included. profiles/k_search_15puzzle_plain_solve_all_launches.txt.
-INSTR_PER_EXPANSION_PLAIN_MIX = 7.65
-# DRAM bytes (read + write) per k_search launch over those launches.
-TRAFFIC_PER_LAUNCH = 1745542
-# Share of k_search's warp instructions that run on the integer ALU pipe
-# (16 lanes per scheduler: one warp instruction every 2 cycles), from ncu
-# over 80 launches of a batched solve
-# (profiles/k_search_15puzzle_batched_pipe_mix.txt). Above one half the ALU
-# pipe, not issue, bounds the kernel: its ceiling is the issue peak divided
-# by 2 x share.
-ALU_PIPE_SHARE = 0.537
+# Instructions per expansion of the search kernel (warp instructions issued
+# per node expanded, ncu smsp__inst_executed.sum / nodes of the captured
+# launches), its share on the integer ALU pipe (16 lanes per scheduler: one
+# warp instruction every 2 cycles, so above one half the ALU pipe, not issue,
+# bounds the kernel at issue peak / (2 x share)), and DRAM bytes (read +
+# write) per launch, for the kernel each form runs.
+#   batched: k_search<4,512,0>, steady-state launches of a batched solve
+#   (profiles/k_search_15puzzle_batched_pipe_mix.txt);
+#   plain: the fused-iteration variant k_search<4,512,1>, the final iteration
+#   of board 0 of perms15_100 as one pass
+#   (profiles/k_search_15puzzle_perms15_board0_final_iteration.txt), and over
+#   every launch of a plain solve of that board, ramp-up and short passes
+#   included (profiles/k_search_15puzzle_plain_solve_all_launches.txt).
+KERNEL_COUNTERS = {
+    "batched": {"kernel": "k_search<4,512,0>", "instr_per_expansion": 5.53, "alu_pipe_share": 0.537,
+                "traffic_per_launch": None},
+    "plain": {"kernel": "k_search<4,512,1>", "instr_per_expansion": 5.86, "alu_pipe_share": 0.537,
+              "traffic_per_launch": 1745542, "instr_per_expansion_all_launches": 7.65},
+}
 
 
 def golden_path(name):
@@ -176,7 +187,7 @@ def run_reference(args, world, rank):
 
     insts = I.WORKLOADS[args.workload]()
     gold = load_golden(args.workload)
-    sample, cores = pick_cpu_sample(insts, gold, args.cpu_sample_nodes)
+    sample, cores = pick_cpu_sample(insts, gold, args.cpu_sample_nodes, args.cpu_sample_board_cap)
     tiles = I.tiles_array([insts[i] for i in sample])
     times, nodes_tot = [], 0
     for step in range(args.warmup + args.steps):
@@ -188,13 +199,13 @@ def run_reference(args, world, rank):
             nodes_tot = sum(r.total_nodes for r in res)
     t = statistics.mean(times)
     value = nodes_tot / t
-    desc = "%d of %d boards (the cheapest by stored oracle node count), %d expansions" % (
-        len(sample), len(insts), nodes_tot)
+    desc = cpu_sample_desc(insts, sample, nodes_tot, args.cpu_sample_board_cap)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-        "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "mode": "CPU oracle, one thread per board"},
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC[args.workload], "mode": "CPU oracle, one thread per board"},
         "instances_per_s": len(sample) / t,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -205,53 +216,30 @@ def run_reference(args, world, rank):
 def run_serving(args):
     """Continuous batching under Poisson arrivals (98% walks of 30-90 moves,
     2% random permutations): completed requests/s and p50/p99 latency from
-    submit to pollable result, per arrival rate."""
+    submit to pollable result, per arrival rate; every result checked against
+    the same boards solved in one batched call."""
     import torch
 
     from paper_1705_02843_gb300 import bpida
 
     torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
     rates = [float(r) for r in args.serving_rates.split(",")]
     out = []
     for rate in rates:
         n_req = int(min(args.serving_max_requests, rate * args.serving_seconds))
-        stream = I.serving_stream(rate, n_req, seed=300000 + int(rate))
-        words = [int(w) for w in I.packed_array([x for _, x in stream])]
-        lat, t_first, t_last = [], None, None
-        with bpida.Server(frontier_bytes=2 << 30, max_slots=8192, time_slice_us=args.serving_slice_us) as sv:
-            t0 = bpida.Server.clock()
-            i = 0
-            got = 0
-            while got < n_req:
-                now = bpida.Server.clock() - t0
-                while i < n_req and stream[i][0] <= now:
-                    sv.submit(words[i], i)
-                    i += 1
-                for r in sv.poll():
-                    if r["status"] != 0:
-                        raise RuntimeError("request %d failed: %s" % (r["req_id"], bpida.status_str(r["status"])))
-                    lat.append(r["latency_s"])
-                    got += 1
-                if i < n_req:
-                    wait = stream[i][0] - (bpida.Server.clock() - t0)
-                    if wait > 0.0005:
-                        time.sleep(min(wait, 0.002))
-                else:
-                    time.sleep(0.0005)
-            t_end = bpida.Server.clock() - t0
-            st = sv.stats()
-        lat.sort()
-        out.append({"rate_per_s": rate, "requests": n_req, "completed_per_s": n_req / t_end,
-                    "p50_ms": 1e3 * lat[len(lat) // 2], "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                    "device_steps": st["steps"], "sliced_steps": st["sliced_steps"], "max_active": st["max_active"],
-                    "wall_s": t_end})
+        summary, results, insts = serve(bpida, rate, n_req, args.serving_slice_us)
+        summary["parity"] = check_served(bpida, torch, dev, results, insts)
+        out.append(summary)
         print(json.dumps(out[-1]), file=sys.stderr, flush=True)
+    best = max(out, key=lambda r: r["completed_per_s"])
     print(json.dumps({"metric": "15-puzzle serving: completed requests/s and p50/p99 latency (submit to result)",
                       "unit": "requests/s", "data": "synthetic",
                       "config": {"workload": "Poisson arrivals; 98% walks of 30-90 moves, 2% random permutations",
                                  "slots": 8192, "mode": "continuous batching",
                                  "time_slice_us": args.serving_slice_us if args.serving_slice_us is not None
                                  else "library default (2000)"},
+                      "saturation": {"completed_per_s": best["completed_per_s"], "at_rate_per_s": best["rate_per_s"]},
                       "rates": out}), flush=True)
 
 
@@ -323,8 +311,8 @@ def run_thread_parallel(args):
     from paper_1705_02843_gb300 import bpida
 
     torch.cuda.set_device(0)
-    insts = I.WORKLOADS[args.workload]()
-    gold = load_golden(args.workload)
+    insts = I.perms15_100()
+    gold = load_golden("perms15_100")
     b = torch.from_numpy(I.packed_array(insts).view(np.int64)).cuda()
     stream = torch.cuda.current_stream()
     names = {bpida.BLOCK_PARALLEL: "this_design", bpida.PSIMPLE: "PSimple", bpida.PSTATICLB: "PStaticLB",
@@ -365,7 +353,7 @@ def run_thread_parallel(args):
     out["this_design"]["speedup_vs_PFullLB"] = out["PFullLB"]["seconds"] / out["this_design"]["seconds"]
     print(json.dumps({"metric": "ablation: thread-parallel IDA* (PSimple, PStaticLB, PFullLB) vs this design, "
                                 "one board per call, exact results",
-                      "config": {"workload": WORKLOAD_DESC}, "unit": "seconds for all boards", "results": out}),
+                      "config": {"workload": WORKLOAD_DESC["perms15_100"]}, "unit": "seconds for all boards", "results": out}),
           flush=True)
 
 
@@ -636,19 +624,390 @@ def run_pdb(args):
     pdb.close()
 
 
-def pick_cpu_sample(insts, gold, budget_nodes):
+def pick_cpu_sample(insts, gold, budget_nodes, board_cap=None):
+    """A bounded sample of a workload for the CPU oracle: the boards in
+    workload order whose stored oracle node count is at most ``board_cap``
+    (None: any), until ``budget_nodes`` expansions; without stored results,
+    the first 8 boards."""
     cores = os.cpu_count() or 1
-    if gold:
-        order = sorted(gold, key=lambda i: sum(gold[i]["nodes"]))
-        sample, acc = [], 0
-        for i in order:
-            c = sum(gold[i]["nodes"])
-            if acc + c > budget_nodes and sample:
+    if not gold:
+        return list(range(min(8, len(insts)))), cores
+    sample, acc = [], 0
+    for i in range(len(insts)):
+        c = sum(gold[i]["nodes"])
+        if board_cap and c > board_cap:
+            continue
+        if acc + c > budget_nodes:
+            if sample:
                 break
-            sample.append(i)
-            acc += c
-        return sample, cores
-    return list(range(min(8, len(insts)))), cores
+            continue
+        sample.append(i)
+        acc += c
+    return sample, cores
+
+
+def pick_cheapest(gold, budget_nodes):
+    """The cheapest boards by stored oracle node count, up to budget_nodes."""
+    order = sorted(gold, key=lambda i: sum(gold[i]["nodes"]))
+    sample, acc = [], 0
+    for i in order:
+        c = sum(gold[i]["nodes"])
+        if acc + c > budget_nodes and sample:
+            break
+        sample.append(i)
+        acc += c
+    return sorted(sample)
+
+
+def cpu_sample_desc(insts, sample, nodes, board_cap):
+    kinds = {}
+    for i in sample:
+        kinds[insts[i].kind] = kinds.get(insts[i].kind, 0) + 1
+    what = ", ".join("%d %ss" % (v, k) for k, v in sorted(kinds.items()))
+    cap = (" among those of at most %.0e stored oracle nodes" % board_cap) if board_cap else ""
+    return "%d of %d boards (%s), taken in workload order%s; %d expansions" % (
+        len(sample), len(insts), what, cap, nodes)
+
+
+def replay(W, tiles, moves):
+    """The board after applying blank moves (0 up, 1 left, 2 right, 3 down)."""
+    b = list(tiles)
+    p = b.index(0)
+    for m in moves:
+        q = p + (-W, -1, 1, W)[m]
+        if not 0 <= q < W * W or (m in (1, 2) and q // W != p // W):
+            return None
+        b[p], b[q] = b[q], b[p]
+        p = q
+    return b
+
+
+def same_as_golden(h, g, first_only=False):
+    """Per-board parity with the stored oracle result (all-solutions mode:
+    length, nodes per iteration, first solution, solution count;
+    first-solution mode: length and every iteration but the last)."""
+    if h["status"] != g["status"]:
+        return False
+    if g["status"] != 0:
+        return True
+    if first_only:
+        return h["length"] == g["length"] and h["nodes"][:-1] == g["nodes"][:-1] and \
+            h["nodes"][-1] <= g["nodes"][-1] and len(h["nodes"]) == len(g["nodes"])
+    return h["length"] == g["length"] and h["nodes"] == g["nodes"] and \
+        "".join(map(str, h["moves"])) == g["moves"] and h["solutions"] == g["solutions"]
+
+
+class Timer:
+    """Steps timed with CUDA events on the launching stream, L2 flushed
+    before each, barrier + synchronize around the timed region."""
+
+    def __init__(self, torch, dev, stream, pg):
+        self.torch, self.dev, self.stream, self.pg = torch, dev, stream, pg
+        self.flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def run(self, step_fn, k, warm):
+        torch = self.torch
+        for _ in range(warm):
+            step_fn()
+        torch.cuda.synchronize(self.dev)
+        if self.pg:
+            self.pg.barrier()
+        ms, aggs, out = [], [], None
+        for _ in range(k):
+            self.flush.fill_(1)
+            torch.cuda.synchronize(self.dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            out, agg = step_fn()
+            e1.record(self.stream)
+            torch.cuda.synchronize(self.dev)
+            ms.append(e0.elapsed_time(e1))
+            # solve calls are asynchronous: their statistics are read once
+            # the stream is idle
+            aggs.append(agg() if callable(agg) else agg)
+        torch.cuda.synchronize(self.dev)
+        if self.pg:
+            self.pg.barrier()
+        return ms, aggs, out
+
+
+AGG_KEYS = ("search_ms", "search_ms_device", "search_nodes", "passes", "launches", "records", "handed_back")
+
+
+def make_steps(bpida, boards, n, cfg):
+    """(batched step, plain step): all boards in one call / one call per board."""
+
+    def stats():
+        st = bpida.last_stats()
+        return {k: st[k] for k in AGG_KEYS}
+
+    def batched():
+        s = bpida.solve(boards, 4, cfg)
+        if s.status != bpida.OK:
+            raise RuntimeError("solve failed: " + bpida.status_str(s.status))
+        return [s], stats
+
+    def plain():
+        sols, agg = [], dict.fromkeys(AGG_KEYS, 0)
+        for i in range(n):
+            s = bpida.solve(boards[i:i + 1], 4, cfg)
+            if s.status != bpida.OK:
+                raise RuntimeError("solve failed: " + bpida.status_str(s.status))
+            sols.append(s)
+        # the calls are asynchronous and statistics are those of the last
+        # call once the stream is idle: the plain step's are not collected
+        return sols, agg
+
+    return batched, plain
+
+
+def hosts_of(sols):
+    return [h for s in sols for h in s.to_host()]
+
+
+def parity(hosts, gold, first_only=False):
+    bad = [i for i, h in enumerate(hosts) if not same_as_golden(h, gold[i], first_only)]
+    return {"checked": len(hosts), "mismatched": len(bad), "first_mismatch": bad[0] if bad else None}
+
+
+def kernel_roofline(bpida, torch, dev, boards, form, clocks, width=4, node_budget=0, counters=None):
+    """Roofline of the search kernel of one form: the solve once more through
+    the host-driven loop, which brackets every search launch with CUDA events
+    on the launching stream; warp instructions per expansion from ncu."""
+    counters = counters or KERNEL_COUNTERS[form]
+    n = boards.shape[0]
+    bpida.set_timing(True)
+    torch.cuda.synchronize(dev)
+    cfg = bpida.make_config(width, driver=1, node_budget=node_budget)
+    ms = nodes = launches = 0
+    if form == "batched":
+        bpida.solve(boards, width, cfg)
+        torch.cuda.synchronize(dev)
+        st = bpida.last_stats()
+        ms, nodes, launches = st["search_ms"], st["search_nodes"], st["passes"]
+    else:
+        for i in range(n):
+            bpida.solve(boards[i:i + 1], width, cfg)
+            torch.cuda.synchronize(dev)
+            st = bpida.last_stats()
+            ms += st["search_ms"]
+            nodes += st["search_nodes"]
+            launches += st["passes"]
+    bpida.set_timing(False)
+    sms = st["sm_count"]
+    f_mhz = clocks.get("sm_mhz") or 2070.0
+    peak = sms * 4 * f_mhz * 1e6 / 1e9  # G warp-instructions issued per second
+    rate = nodes / (ms / 1e3)
+    I_exp = counters["instr_per_expansion"]
+    achieved = rate * I_exp / 1e9
+    share = counters["alu_pipe_share"]
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s", "frac": achieved / peak,
+            "traffic": counters.get("traffic_per_launch"), "kernel": counters["kernel"],
+            "instr_per_expansion": I_exp, "expansions_per_s_in_kernel": rate,
+            "launch_ms_mean": ms / max(launches, 1), "launches_timed": launches, "nodes_timed": nodes,
+            "peak_basis": "%d SMs x 4 schedulers x %.0f MHz median SM clock sampled during the run" % (sms, f_mhz),
+            "alu_pipe": {"share": share, "peak": peak / (2 * share), "frac": achieved / (peak / (2 * share)),
+                         "basis": "the integer ALU pipe takes a warp instruction every 2 cycles per scheduler; "
+                                  "with this share of ALU instructions it caps issue at 1 / (2 x share) per cycle"}}
+    if counters.get("instr_per_expansion_all_launches"):
+        roof["issue_utilization_all_launches"] = rate * counters["instr_per_expansion_all_launches"] / 1e9 / peak
+    return roof
+
+
+def serve(bpida, rate, n_req, slice_us=None, seed=None):
+    """Drives the continuous-batching service with a Poisson stream; returns
+    (summary, results by request id, boards)."""
+    stream = I.serving_stream(rate, n_req, seed=300000 + int(rate) if seed is None else seed)
+    words = [int(w) for w in I.packed_array([x for _, x in stream])]
+    lat, results = [], {}
+    with bpida.Server(frontier_bytes=2 << 30, max_slots=8192, time_slice_us=slice_us) as sv:
+        t0 = bpida.Server.clock()
+        i = got = 0
+        while got < n_req:
+            now = bpida.Server.clock() - t0
+            while i < n_req and stream[i][0] <= now:
+                sv.submit(words[i], i)
+                i += 1
+            for r in sv.poll():
+                if r["status"] != 0:
+                    raise RuntimeError("request %d failed: %s" % (r["req_id"], bpida.status_str(r["status"])))
+                lat.append(r["latency_s"])
+                results[r["req_id"]] = r
+                got += 1
+            if i < n_req:
+                wait = stream[i][0] - (bpida.Server.clock() - t0)
+                if wait > 0.0005:
+                    time.sleep(min(wait, 0.002))
+            else:
+                time.sleep(0.0005)
+        t_end = bpida.Server.clock() - t0
+        st = sv.stats()
+    lat.sort()
+    summary = {"rate_per_s": rate, "requests": n_req, "completed_per_s": n_req / t_end,
+               "p50_ms": 1e3 * lat[len(lat) // 2], "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+               "device_steps": st["steps"], "sliced_steps": st["sliced_steps"], "max_active": st["max_active"],
+               "wall_s": t_end, "arrivals_s": stream[-1][0]}
+    return summary, results, [x for _, x in stream]
+
+
+def check_served(bpida, torch, dev, results, insts):
+    """Every served result equals the same board's result from one batched
+    solve call (which the parity tests check against the oracle) and replays
+    to the goal."""
+    b = torch.from_numpy(I.packed_array(insts).view(np.int64)).to(dev)
+    ref = bpida.solve(b, 4).to_host()
+    bad = 0
+    for i, x in enumerate(insts):
+        r, h = results[i], ref[i]
+        if (r["length"], r["nodes"], r["moves"], r["solutions"]) != (h["length"], h["nodes"], h["moves"],
+                                                                       h["solutions"]) or \
+                replay(4, x.tiles, r["moves"]) != list(range(16)):
+            bad += 1
+    return {"checked": len(insts), "mismatched": bad,
+            "against": "the same boards solved in one batched call, and a replay of every solution"}
+
+
+def leg_perms(bpida, torch, dev, timer, steps, clocks_hint):
+    """perms15_100 (the paper-shaped workload): plain and batched, parity
+    against the stored oracle results, and the plain form's search-kernel
+    roofline."""
+    insts = I.perms15_100()
+    gold = load_golden("perms15_100")
+    n = len(insts)
+    boards = torch.from_numpy(I.packed_array(insts).view(np.int64)).to(dev)
+    batched, plain = make_steps(bpida, boards, n, bpida.make_config(4))
+    ms_p, _, psols = timer.run(plain, steps, 1)
+    ms_b, _, bsols = timer.run(batched, steps, 1)
+    hp, hb = hosts_of(psols), hosts_of(bsols)
+    exp = sum(sum(h["nodes"]) for h in hp)
+    t_p, t_b = sum(ms_p) / 1e3 / steps, sum(ms_b) / 1e3 / steps
+    par = parity(hp, gold)
+    pb = parity(hb, gold)
+    par["mismatched"] += pb["mismatched"]
+    par["checked"] += pb["checked"]
+    return {"workload": WORKLOAD_DESC["perms15_100"], "expansions_per_step": exp, "steps": steps,
+            "plain": {"expansions_per_s": exp / t_p, "instances_per_s": n / t_p, "ms_per_step": t_p * 1e3},
+            "batched": {"expansions_per_s": exp / t_b, "instances_per_s": n / t_b, "ms_per_step": t_b * 1e3},
+            "batched_over_plain_instances_per_s": t_p / t_b,
+            "parity": par,
+            "roofline_plain": kernel_roofline(bpida, torch, dev, boards, "plain", clocks_hint)}
+
+
+# 24-puzzle search kernel k_search<5,512,0>: warp instructions per expansion
+# of the final iteration of walk 406 of walks24_1024 (39.7M nodes, one pass,
+# ncu smsp__inst_executed.sum / nodes).
+KERNEL_COUNTERS_W5 = {"kernel": "k_search<5,512,0>", "instr_per_expansion": 10.2, "alu_pipe_share": 0.5,
+                      "traffic_per_launch": None}
+
+
+def leg_walks24(bpida, torch, dev, timer, steps, clocks_hint):
+    """walks24_1024: 1024 24-puzzle walks of 40-100 moves, batched, with the
+    oracle's node budget of 5e7 nodes per board; parity against the stored
+    oracle results (a board stopped by the budget reports its completed
+    iterations)."""
+    insts = I.walks24_1024()
+    gold = load_golden("walks24_1024")
+    n = len(insts)
+    budget = 50_000_000
+    boards = torch.from_numpy(I.packed_array(insts).view(np.int64).reshape(n, 2)).to(dev)
+    cfg = bpida.make_config(5, node_budget=budget)
+
+    def step():
+        s = bpida.solve(boards, 5, cfg)
+        if s.status != bpida.OK:
+            raise RuntimeError("solve failed: " + bpida.status_str(s.status))
+        return [s], lambda: {"search_nodes": bpida.last_stats()["search_nodes"]}
+
+    ms, aggs, sols = timer.run(step, steps, 1)
+    hosts = hosts_of(sols)
+    bad = 0
+    for i, h in enumerate(hosts):
+        g = gold[i]
+        want = g["nodes"] if g["status"] == 0 else g["nodes"][:-1]
+        if h["status"] != g["status"] or h["nodes"] != want or (
+                g["status"] == 0 and (h["length"] != g["length"] or "".join(map(str, h["moves"])) != g["moves"])):
+            bad += 1
+    t = sum(ms) / 1e3 / steps
+    reported = sum(sum(h["nodes"]) for h in hosts)
+    searched = aggs[-1]["search_nodes"]
+    roof = kernel_roofline(bpida, torch, dev, boards, "batched", clocks_hint, width=5, node_budget=budget,
+                           counters=KERNEL_COUNTERS_W5)
+    return {"workload": "walks24_1024: 1024 seeded 24-puzzle random walks of 40-100 moves (seeds 200000-201023), "
+                        "node budget 5e7 per board (as the oracle's)",
+            "solved_within_budget": sum(1 for h in hosts if h["status"] == 0), "boards": n,
+            "ms_per_step": t * 1e3, "instances_per_s": n / t,
+            "reported_expansions_per_s": reported / t,
+            "searched_expansions_per_s": searched / t,
+            "note": "reported = the nodes of the iterations each board completed (what the oracle reports); "
+                    "searched = every node the search kernel popped, the iterations the budget cut short included",
+            "parity": {"checked": n, "mismatched": bad, "against": "tests/golden/walks24_1024.json"},
+            "roofline": roof}
+
+
+def leg_serving(bpida, torch, dev, rates, n_req):
+    out = []
+    for rate in rates:
+        summary, results, insts = serve(bpida, rate, n_req)
+        summary["parity"] = check_served(bpida, torch, dev, results, insts)
+        out.append(summary)
+    return {"workload": "Poisson arrivals; 98% walks of 30-90 moves, 2% random permutations; "
+                        "latency from submit to pollable result", "mode": "continuous batching, 2 ms time slices",
+            "rates": out}
+
+
+def leg_first_solution(bpida, torch, dev, budget_nodes):
+    """First-solution mode (count_all = 0, Section 6's main timing
+    experiment) against the oracle's first-solution mode on one host core
+    (the paper's sequential-solver setting), and the same for all-solutions
+    mode (its count-all experiment), on the cheapest boards of perms15_100;
+    one board per solve call on the GPU, as in the paper."""
+    import oracle
+
+    insts = I.perms15_100()
+    gold = load_golden("perms15_100")
+    idx = pick_cheapest(gold, budget_nodes)
+    sub = [insts[i] for i in idx]
+    boards = torch.from_numpy(I.packed_array(sub).view(np.int64)).to(dev)
+    tiles = I.tiles_array(sub)
+    out = {"boards": len(idx), "sample": "the %d cheapest boards of perms15_100 (stored all-solutions node count, "
+                                         "%d nodes in all)" % (len(idx), sum(sum(gold[i]["nodes"]) for i in idx))}
+    stream = torch.cuda.current_stream(dev)
+    for mode, count_all in (("first_solution", False), ("all_solutions", True)):
+        cfg = bpida.make_config(4, count_all=count_all)
+        for i in range(len(idx)):  # warm-up (graphs, workspace)
+            bpida.solve(boards[i:i + 1], 4, cfg)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sols = [bpida.solve(boards[i:i + 1], 4, cfg) for i in range(len(idx))]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t_gpu = e0.elapsed_time(e1) / 1e3
+        t0 = time.perf_counter()
+        ref = oracle.solve_batch(4, tiles, count_all=count_all, nthreads=1)
+        t_cpu = time.perf_counter() - t0
+        hosts = hosts_of(sols)
+        bad = 0
+        for x, h, r in zip(sub, hosts, ref):
+            ok = h["status"] == 0 and h["length"] == r.length and h["nodes"][:-1] == r.nodes[:-1] and \
+                len(h["nodes"]) == len(r.nodes) and replay(4, x.tiles, h["moves"]) == list(range(16))
+            if count_all:
+                ok = ok and h["nodes"] == r.nodes and h["moves"] == r.moves
+            bad += 0 if ok else 1
+        out[mode] = {"gpu_s": t_gpu, "cpu_one_core_s": t_cpu, "speedup": t_cpu / t_gpu,
+                     "gpu_instances_per_s": len(idx) / t_gpu, "cpu_instances_per_s": len(idx) / t_cpu,
+                     "gpu_expansions": sum(sum(h["nodes"]) for h in hosts),
+                     "cpu_expansions": sum(r.total_nodes for r in ref),
+                     "parity": {"checked": len(idx), "mismatched": bad,
+                                "against": "the oracle's %s mode on the same boards (length, %s, replay)" % (
+                                    "first-solution" if not count_all else "all-solutions",
+                                    "every iteration but the last" if not count_all
+                                    else "every iteration, first solution")}}
+    out["paper"] = "Section 6: 4.98x (first solution) and 6.78x (all solutions) over one Xeon E5-2670 core, on a " \
+                   "GRID K520, Korf's 100 boards (context only)"
+    return out
 
 
 def main():
@@ -657,9 +1016,16 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="perms15_100", choices=["perms15_100"])
+    ap.add_argument("--workload", default="mixed15_4096", choices=["mixed15_4096", "perms15_100"])
+    ap.add_argument("--plain-steps", type=int, default=3,
+                    help="timed steps of the plain form (one call per board; slower, so fewer)")
+    ap.add_argument("--sub-steps", type=int, default=3, help="timed steps of each sub-workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-nodes", type=float, default=1.5e9)
+    ap.add_argument("--no-sub", action="store_true", help="skip the sub-workload legs")
+    ap.add_argument("--cpu-sample-nodes", type=float, default=8e8)
+    ap.add_argument("--cpu-sample-board-cap", type=float, default=5e7)
+    ap.add_argument("--first-solution-nodes", type=float, default=3e8,
+                    help="all-solutions node count of the boards the first-solution leg runs on one core")
     ap.add_argument("--ablation", action="store_true",
                     help="compare against the paper's BPIDA* kernel instead")
     ap.add_argument("--workloads", action="store_true",
@@ -673,6 +1039,9 @@ def main():
     ap.add_argument("--serving-max-requests", type=int, default=20000)
     ap.add_argument("--serving-slice-us", type=int, default=None,
                     help="time slice of a device step in microseconds (0 = none; default: the library's)")
+    ap.add_argument("--sub-serving-rates", default="2000,10000,50000",
+                    help="arrival rates of the default line's serving leg")
+    ap.add_argument("--sub-serving-requests", type=int, default=4000)
     ap.add_argument("--pdb", default=None, choices=sorted(I.PDB_PARTITIONS),
                     help="time the pattern-database heuristic with this tile partition")
     ap.add_argument("--profile-pdb", type=int, default=None, metavar="IDX",
@@ -762,257 +1131,147 @@ def main():
         print(json.dumps({"profile_case": args.profile_case, "status": s.status, "length": h["length"],
                           "iters": h["iters"], "nodes": h["nodes"], "stats": st}), flush=True)
         return
+
     n = len(insts)
+    gold = load_golden(args.workload)
     packed = I.packed_array(insts)
     boards = torch.from_numpy(packed.view(np.int64)).to(dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    bpida.set_timing(True)
-
+    timer = Timer(torch, dev, stream, pg)
     base_cfg = bpida.make_config(4, driver=1 if args.driver == "host" else 0)
-
-    def plain_step(cfg=None):
-        cfg = cfg if cfg is not None else base_cfg
-        sols, agg = [], {"search_ms": 0.0, "search_ms_device": 0.0, "search_nodes": 0, "passes": 0,
-                         "launches": 0, "records": 0, "handed_back": 0}
-        for i in range(n):
-            s = bpida.solve(boards[i:i + 1], 4, cfg)
-            if s.status != bpida.OK:
-                raise RuntimeError("solve failed: " + bpida.status_str(s.status))
-            st = bpida.last_stats()
-            for k in agg:
-                agg[k] += st[k]
-            sols.append(s)
-        return sols, agg
-
-    def batched_step():
-        s = bpida.solve(boards, 4, base_cfg)
-        if s.status != bpida.OK:
-            raise RuntimeError("solve failed: " + bpida.status_str(s.status))
-        st = bpida.last_stats()
-        return [s], {k: st[k] for k in ("search_ms", "search_ms_device", "search_nodes", "passes", "launches",
-                                        "records", "handed_back")}
-
-    def expansions(sols):
-        tot = 0
-        for s in sols:
-            tot += int(s.nodes.cpu().numpy().view(np.uint64).sum())
-        return tot
-
-    def timed(step_fn, k, warm):
-        for _ in range(warm):
-            step_fn()
-        torch.cuda.synchronize(dev)
-        if pg:
-            pg.barrier()
-        ms, aggs, sols = [], [], None
-        for _ in range(k):
-            flush.fill_(1)
-            torch.cuda.synchronize(dev)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            sols, agg = step_fn()
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            ms.append(e0.elapsed_time(e1))
-            aggs.append(agg)
-        torch.cuda.synchronize(dev)
-        if pg:
-            pg.barrier()
-        return ms, aggs, sols
-
-    # parity of this run's results against the stored oracle results
-    gold = load_golden(args.workload)
-    sols, _ = plain_step()
-    checked = mismatched = 0
-    if gold:
-        for i, s in enumerate(sols):
-            if i in gold:
-                h = s.to_host()[0]
-                g = gold[i]
-                checked += 1
-                if h["length"] != g["length"] or h["nodes"] != g["nodes"] or "".join(map(str, h["moves"])) != g["moves"]:
-                    mismatched += 1
-    exp_per_step = expansions(sols)
-
-    with ClockSampler(local) as clk:
-        ms_plain, agg_plain, _ = timed(plain_step, args.steps, args.warmup)
-        ms_batch, agg_batch, bsols = timed(batched_step, args.steps, 1)
-    clocks = clk.summary()
-    if expansions(bsols) != exp_per_step:
-        raise RuntimeError("batched and plain expansions differ")
-
-    # first-solution mode (Section 6's main timing experiment): each board
-    # stops at its first optimal solution
-    first_cfg = bpida.make_config(4, count_all=False, driver=1 if args.driver == "host" else 0)
-
-    def first_plain_step():
-        sols = []
-        for i in range(n):
-            s = bpida.solve(boards[i:i + 1], 4, first_cfg)
-            if s.status != bpida.OK:
-                raise RuntimeError("solve failed: " + bpida.status_str(s.status))
-            sols.append(s)
-        return sols, {}
-
-    def first_batched_step():
-        s = bpida.solve(boards, 4, first_cfg)
-        if s.status != bpida.OK:
-            raise RuntimeError("solve failed: " + bpida.status_str(s.status))
-        return [s], {}
-
-    ms_fp, _, fsols = timed(first_plain_step, max(1, args.steps // 2), 1)
-    ms_fb, _, _ = timed(first_batched_step, max(1, args.steps // 2), 1)
-    first_exp = expansions(fsols)
-
-    # end to end through the host-buffer path (pinned boards, results back)
-    host_boards = torch.from_numpy(packed.view(np.int64)).pin_memory()
-    ml, mi = bpida.max_len(4), bpida.max_iters(4)
-    h2d = host_boards.numel() * 8
-    d2h = n * (4 + ml + 8 * mi + 4 + 4)
-    host_out = {k: torch.empty(sz, dtype=dt).pin_memory() for k, sz, dt in (
-        ("len", n, torch.int32), ("moves", n * ml, torch.uint8), ("nodes", n * mi, torch.int64),
-        ("iters", n, torch.int32), ("status", n, torch.int32))}
-
-    def e2e_step():
-        dboards = host_boards.to(dev, non_blocking=True)
-        sols = []
-        for i in range(n):
-            s = bpida.solve(dboards[i:i + 1], 4, base_cfg)
-            if s.status != bpida.OK:
-                raise RuntimeError(bpida.status_str(s.status))
-            sols.append(s)
-        host_out["len"].copy_(torch.cat([s.length for s in sols]), non_blocking=True)
-        host_out["moves"].copy_(torch.cat([s.moves.reshape(-1) for s in sols]), non_blocking=True)
-        host_out["nodes"].copy_(torch.cat([s.nodes.reshape(-1) for s in sols]), non_blocking=True)
-        host_out["iters"].copy_(torch.cat([s.iters for s in sols]), non_blocking=True)
-        host_out["status"].copy_(torch.cat([s.inst_status for s in sols]), non_blocking=True)
-        return sols, {}
-
-    ms_e2e, _, _ = timed(e2e_step, max(1, args.steps), 1)
-    e2e_exp = int(host_out["nodes"].numpy().view(np.uint64).sum())
-    if e2e_exp != exp_per_step:
-        raise RuntimeError("end-to-end expansions differ")
+    batched_step, plain_step = make_steps(bpida, boards, n, base_cfg)
+    k = args.steps
 
     def mx(v):
         return max_over_ranks(v, pg, dev)
 
-    t_plain = mx(sum(ms_plain)) / 1e3
-    t_batch = mx(sum(ms_batch)) / 1e3
-    t_e2e = mx(sum(ms_e2e)) / 1e3
-    k = args.steps
-    value = world * exp_per_step * k / t_plain
-    inst_s = world * n * k / t_plain
-    b_value = world * exp_per_step * k / t_batch
-    e2e_value = world * exp_per_step * len(ms_e2e) / t_e2e
+    # headline: the batched form, K timed steps
+    with ClockSampler(local) as clk:
+        ms_b, agg_b, bsols = timer.run(batched_step, k, args.warmup)
+    clocks = clk.summary()
+    hb = hosts_of(bsols)
+    exp_per_step = sum(sum(h["nodes"]) for h in hb)
+    par_b = parity(hb, gold) if gold else None
+    t_batch = mx(sum(ms_b)) / 1e3
+    value = world * exp_per_step * k / t_batch
+    inst_s = world * n * k / t_batch
 
-    # roofline of the dominant kernel (k_search): one more plain step with
-    # the host-driven loop, which brackets every k_search launch with CUDA
-    # events on the launching stream
-    torch.cuda.synchronize(dev)
-    _, agg_ev = plain_step(bpida.make_config(4, driver=1))
-    s_ms = agg_ev["search_ms"]
-    s_nodes = agg_ev["search_nodes"]
-    s_launch = agg_ev["passes"]
-    # the timed (graph-driven) steps: k_search time from the device clock
-    dev_ms = sum(a["search_ms_device"] for a in agg_plain)
-    dev_nodes = sum(a["search_nodes"] for a in agg_plain)
-    launches = sum(a["launches"] for a in agg_plain) // k
-    sms = bpida.last_stats()["sm_count"]
-    f_mhz = clocks["sm_mhz"] or 1455.0
-    peak = sms * 4 * f_mhz * 1e6 / 1e9  # warp-instructions issued, G/s
-    roof = None
-    if INSTR_PER_EXPANSION:
-        achieved = s_nodes * INSTR_PER_EXPANSION / (s_ms / 1e3) / 1e9
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
-                "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH,
-                "kernel": "k_search<4,512,1>", "instr_per_expansion": INSTR_PER_EXPANSION,
-                "launch_ms_mean": s_ms / max(s_launch, 1), "launches_timed": s_launch,
-                "issue_utilization_plain_mix": s_nodes * INSTR_PER_EXPANSION_PLAIN_MIX / (s_ms / 1e3) / 1e9 / peak,
-                "expansions_per_s_in_kernel": s_nodes / (s_ms / 1e3),
-                "expansions_per_s_in_kernel_timed_steps": dev_nodes / (dev_ms / 1e3) if dev_ms else None,
-                "peak_basis": "%d SMs x 4 schedulers x %.0f MHz median SM clock sampled during the run" % (sms, f_mhz),
-                "alu_pipe": {"share": ALU_PIPE_SHARE, "peak": peak / (2 * ALU_PIPE_SHARE),
-                             "frac": achieved / (peak / (2 * ALU_PIPE_SHARE)),
-                             "basis": "the integer ALU pipe takes a warp instruction every 2 cycles per "
-                                      "scheduler; with this share of ALU instructions it caps issue at "
-                                      "1 / (2 x share) per cycle"}}
-    else:
-        roof = {"bound": "alu", "achieved": None, "peak": peak, "unit": "Gwarp-inst/s", "frac": None,
-                "traffic": None, "kernel": "k_search<4,512,1>",
-                "launch_ms_mean": s_ms / max(s_launch, 1), "launches_timed": s_launch,
-                "expansions_per_s_in_kernel": s_nodes / (s_ms / 1e3) if s_ms else None,
-                "expansions_per_s_in_kernel_timed_steps": dev_nodes / (dev_ms / 1e3) if dev_ms else None}
+    # the plain form: one call per board, fewer timed steps
+    kp = max(1, min(args.plain_steps, k))
+    ms_p, _, psols = timer.run(plain_step, kp, 1)
+    hp = hosts_of(psols)
+    if sum(sum(h["nodes"]) for h in hp) != exp_per_step:
+        raise RuntimeError("batched and plain expansions differ")
+    par_p = parity(hp, gold) if gold else None
+    t_plain = mx(sum(ms_p)) / 1e3
+    plain_inst_s = world * n * kp / t_plain
+
+    # end to end through the host-buffer path: pinned boards copied in and
+    # every result copied back inside the timed region (batched form)
+    host_boards = torch.from_numpy(packed.view(np.int64)).pin_memory()
+    ml, mi = bpida.max_len(4), bpida.max_iters(4)
+    host_out = {key: torch.empty(sz, dtype=dt).pin_memory() for key, sz, dt in (
+        ("len", n, torch.int32), ("moves", n * ml, torch.uint8), ("nodes", n * mi, torch.int64),
+        ("iters", n, torch.int32), ("status", n, torch.int32), ("solutions", n, torch.int64))}
+    h2d = host_boards.numel() * 8
+    d2h = sum(t.numel() * t.element_size() for t in host_out.values())
+
+    def e2e_step():
+        dboards = host_boards.to(dev, non_blocking=True)
+        s = bpida.solve(dboards, 4, base_cfg)
+        if s.status != bpida.OK:
+            raise RuntimeError(bpida.status_str(s.status))
+        host_out["len"].copy_(s.length, non_blocking=True)
+        host_out["moves"].copy_(s.moves.reshape(-1), non_blocking=True)
+        host_out["nodes"].copy_(s.nodes.reshape(-1), non_blocking=True)
+        host_out["iters"].copy_(s.iters, non_blocking=True)
+        host_out["status"].copy_(s.inst_status, non_blocking=True)
+        host_out["solutions"].copy_(s.solutions, non_blocking=True)
+        return [s], {}
+
+    ms_e2e, _, _ = timer.run(e2e_step, k, 1)
+    if int(host_out["nodes"].numpy().view(np.uint64).sum()) != exp_per_step:
+        raise RuntimeError("end-to-end expansions differ")
+    t_e2e = mx(sum(ms_e2e)) / 1e3
+    e2e_value = world * exp_per_step * k / t_e2e
+
+    # roofline of the dominant kernel (the batched form's k_search)
+    roof = kernel_roofline(bpida, torch, dev, boards, "batched", clocks)
+    dev_ms = sum(a["search_ms_device"] for a in agg_b)
+    dev_nodes = sum(a["search_nodes"] for a in agg_b)
+    roof["expansions_per_s_in_kernel_timed_steps"] = dev_nodes / (dev_ms / 1e3) if dev_ms else None
+    roof["search_share_of_step"] = dev_ms / sum(ms_b) if dev_ms else None
 
     # HBM traffic of the frontiers and the hand-back queue (the only DRAM
     # traffic of the method: a subtree's search stays in shared memory): each
     # 24-byte record is written once and read once
-    rec_bytes = 24
-    fq_bytes = 2 * rec_bytes * sum(a["records"] + a["handed_back"] for a in agg_plain) / k
+    fq_bytes = 2 * 24 * sum(a["records"] + a["handed_back"] for a in agg_b) / k
     hbm_peak = None
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             hbm_peak = float(json.load(f)["hbm_gbs"])
     except (OSError, ValueError, KeyError):
         pass
-    fq_gbs = fq_bytes / (t_plain / k) / 1e9
+    fq_gbs = fq_bytes / (t_batch / k) / 1e9
     hbm = {"bytes_per_step": fq_bytes, "gbs": fq_gbs, "peak_gbs": hbm_peak,
            "frac": fq_gbs / hbm_peak if hbm_peak else None,
            "what": "frontier records (splitter writes, first pass reads) and hand-back queue records, "
-                   "24 B each, written once and read once, plain form"}
+                   "24 B each, written once and read once, batched form"}
+
+    sub = {}
+    if rank == 0 and not args.no_sub:
+        ks = max(1, args.sub_steps)
+        if args.workload != "perms15_100":
+            sub["perms15_100"] = leg_perms(bpida, torch, dev, timer, ks, clocks)
+        sub["walks24_1024"] = leg_walks24(bpida, torch, dev, timer, ks, clocks)
+        sub["serving"] = leg_serving(bpida, torch, dev, [float(r) for r in args.sub_serving_rates.split(",")],
+                                     args.sub_serving_requests)
+        if world == 1:
+            sub["first_solution"] = leg_first_solution(bpida, torch, dev, args.first_solution_nodes)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
 
-        sample, cores = pick_cpu_sample(insts, gold, args.cpu_sample_nodes)
+        sample, cores = pick_cpu_sample(insts, gold, args.cpu_sample_nodes, args.cpu_sample_board_cap)
         t0 = time.perf_counter()
         res = oracle.solve_batch(4, I.tiles_array([insts[i] for i in sample]), count_all=True, nthreads=cores)
         dt = time.perf_counter() - t0
         cn = sum(r.total_nodes for r in res)
-        # one thread (the paper's sequential-solver setting) on the cheapest
-        # boards up to ~1e8 nodes
-        one, _ = pick_cpu_sample(insts, gold, args.cpu_sample_nodes / 16)
-        t1 = time.perf_counter()
-        res1 = oracle.solve_batch(4, I.tiles_array([insts[i] for i in one]), count_all=True, nthreads=1)
-        dt1 = time.perf_counter() - t1
-        cn1 = sum(r.total_nodes for r in res1)
         cpu = {"value": cn / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "%d of %d boards (cheapest by stored oracle node count), %d expansions, %.1f s" % (
-                   len(sample), n, cn, dt),
+               "sample": cpu_sample_desc(insts, sample, cn, args.cpu_sample_board_cap) + ", %.1f s" % dt,
                "instances_per_s": len(sample) / dt,
-               "single_thread": {"value": cn1 / dt1, "unit": UNIT, "cores": 1,
-                                 "sample": "%d cheapest boards, %d expansions, %.1f s" % (len(one), cn1, dt1)}}
+               "note": "instances/s of the sample only: its boards are cheaper than the workload's average, so "
+                       "this is not comparable with the GPU's instances/s over the whole workload"}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": k,
-            "warmup": args.warmup, "ms_per_step": t_plain * 1e3 / k, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": t_batch * 1e3 / k, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC, "mode": "plain: one solve call per board",
+            "config": {"workload": WORKLOAD_DESC[args.workload],
+                       "mode": "batched: all %d boards in one solve call" % n,
                        "driver": args.driver,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "flushed between steps (256 MiB write)"},
             "instances_per_s": inst_s,
             "expansions_per_step": exp_per_step,
-            "batched": {"value": b_value, "unit": UNIT, "instances_per_s": world * n * k / t_batch,
-                        "ms_per_step": t_batch * 1e3 / k, "mode": "all 100 boards in one solve call"},
-            "first_solution": {"mode": "stop at the first optimal solution",
-                               "plain_instances_per_s": world * n * len(ms_fp) / (mx(sum(ms_fp)) / 1e3),
-                               "batched_instances_per_s": world * n * len(ms_fb) / (mx(sum(ms_fb)) / 1e3),
-                               "plain_expansions_per_step": first_exp},
-            "parity": {"checked": checked, "mismatched": mismatched,
-                       "against": "stored oracle results (length, per-iteration nodes, first solution)"},
+            "plain": {"value": world * exp_per_step * kp / t_plain, "unit": UNIT, "instances_per_s": plain_inst_s,
+                      "ms_per_step": t_plain * 1e3 / kp, "steps": kp, "mode": "one solve call per board"},
+            "batched_over_plain_instances_per_s": inst_s / plain_inst_s,
+            "parity": {"batched": par_b, "plain": par_p,
+                       "against": "tests/golden/%s.json: stored oracle results (length, nodes per iteration, "
+                                  "first solution, solution count) of every board" % args.workload},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": t_e2e * 1e3 / len(ms_e2e)},
+                    "ms_per_step": t_e2e * 1e3 / k, "instances_per_s": world * n * k / t_e2e},
             "roofline": roof,
             "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                        "reasons": clocks["reasons"]},
-            "gpu_launches": launches * k,
+            "gpu_launches": sum(a["launches"] for a in agg_b),
             "hbm_frontier_queue": hbm,
             "cpu_baseline": cpu,
         }
+        line.update(sub)
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()

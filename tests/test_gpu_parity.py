@@ -410,3 +410,38 @@ def test_fused_step_cap_does_not_change_results(cap):
             check_against(4, [t], got, [r])
     finally:
         bpida.set_fuse_nodes(0)
+
+
+def test_bpida_solve_default_entry_point():
+    """bpida_solve, the call of the problem statement with the default
+    configuration, called directly through the C ABI (no configuration
+    struct, no per-instance status): 16 walks and two random permutations
+    of the 4096-board mix against the oracle and the stored oracle results."""
+    import ctypes
+
+    lib = bpida.load()
+    doc = {r["index"]: r for r in _golden("mixed15_4096")["instances"]}
+    mix = I.mixed15_4096()
+    insts = I.walks15_16x40() + [mix[20], mix[40]]
+    n = len(insts)
+    boards = torch.from_numpy(I.packed_array(insts).view(np.int64)).to("cuda:0")
+    ml, mi = bpida.max_len(4), bpida.max_iters(4)
+    out_len = torch.full((n,), -7, dtype=torch.int32, device="cuda:0")
+    out_moves = torch.full((n, ml), 9, dtype=torch.uint8, device="cuda:0")
+    out_nodes = torch.full((n, mi), -1, dtype=torch.int64, device="cuda:0")
+    stream = torch.cuda.current_stream()
+    rc = lib.bpida_solve(ctypes.c_void_p(boards.data_ptr()), n, ctypes.c_void_p(out_len.data_ptr()),
+                         ctypes.c_void_p(out_moves.data_ptr()), ctypes.c_void_p(out_nodes.data_ptr()),
+                         ctypes.c_void_p(stream.cuda_stream))
+    torch.cuda.synchronize()
+    assert rc == bpida.OK
+    L = out_len.cpu().tolist()
+    mv = out_moves.cpu().numpy()
+    nd = out_nodes.cpu().numpy().view(np.uint64)
+    ref = oracle.solve_batch(4, I.tiles_array(insts[:16]), count_all=True)
+    want = [(r.length, r.nodes, "".join(map(str, r.moves))) for r in ref] + \
+        [(doc[i]["length"], doc[i]["nodes"], doc[i]["moves"]) for i in (20, 40)]
+    for i, (length, nodes, moves) in enumerate(want):
+        assert L[i] == length
+        assert [int(x) for x in nd[i, :len(nodes)]] == nodes and not nd[i, len(nodes):].any()
+        assert "".join(str(int(x)) for x in mv[i, :length]) == moves and not mv[i, length:].any()
