@@ -35,14 +35,34 @@
  *
  * Streams and ownership: every pointer argument of the solve calls is
  * DEVICE memory owned by the caller; the library keeps no reference after
- * returning. Work is issued on `stream` and the call returns once the
- * results are written (it synchronises `stream` before returning). The
- * library owns a per-device workspace that it grows on demand and frees in
- * bpida_release_workspace(); calls are serialised by a process-wide lock.
+ * the call's work has finished. The solve calls are stream-ordered and
+ * asynchronous: with the default driver (driver = 0) a call enqueues its
+ * work on `stream` and returns without waiting for it; the inputs must stay
+ * valid and the outputs untouched until the stream has reached the end of
+ * the call's work (synchronise the stream, or order later work after it).
+ * Calls on the same stream run one after another; calls on different
+ * streams may overlap on the device. Each call takes a workspace from a
+ * per-device pool of at most four (grown on demand, freed by
+ * bpida_release_workspace()): the one last used on the same stream, else
+ * an idle one, else a new one; with four busy on other streams the call's
+ * stream waits on the device for the least recently used one. The first
+ * call with a new configuration or a larger batch may allocate device
+ * memory and build a CUDA graph, and a call that has to grow a busy
+ * workspace waits for that workspace's last call first. The host-driven
+ * loop (driver = 1), the thread-parallel variants (2-4) and
+ * bpida_solve_noalloc synchronise `stream` before returning. The library
+ * serialises its host-side bookkeeping with a process-wide lock, held while
+ * a call is enqueued.
  *
  * Errors: arguments the host can check are rejected synchronously with
- * BPIDA_EINVAL before any work is issued. Per-instance problems are
- * reported in out_status[i] and do not stop the other instances. The
+ * BPIDA_EINVAL before any work is issued, and a failed CUDA runtime call
+ * returns BPIDA_ECUDA (BPIDA_ENOMEM for a failed allocation). What the
+ * device finds is reported per instance once the work has finished:
+ * out_status[i] (bpida_solve_ex) and out_len[i] = -1 for an unsolvable
+ * board, a node budget or length cap that ran out, and, for every instance
+ * not finished when a call-wide problem stopped the search (hand-back
+ * queue capacity: BPIDA_ENOMEM; a failed internal check: BPIDA_EINTERNAL),
+ * that problem. Per-instance problems do not stop the other instances. The
  * library never calls __trap() or a device assert.
  */
 #ifndef BPIDA_H
@@ -164,10 +184,11 @@ int bpida_max_iters(int width);  /* iterations per node-count row */
  *                      the order up < left < right < down), zero-filled
  *   out_nodes_per_iter device, n * bpida_max_iters(4) uint64: nodes
  *                      expanded in each iteration, zero-filled
- * Returns BPIDA_OK unless the call itself failed (a bad argument, a CUDA
- * error, workspace or queue capacity, an internal check); what happened to
- * each instance (solved, unsolvable board, length cap, node budget) is its
- * out_len / out_status entry (bpida_solve_ex).
+ * Returns BPIDA_OK once the work is enqueued on `stream` (the results are
+ * written when the stream reaches the end of it), or the error of a call
+ * that could not be issued (a bad argument, a CUDA error, device memory).
+ * An instance with out_len -1 was not solved (its reason is its
+ * bpida_solve_ex out_status entry).
  */
 bpida_status bpida_solve(const uint64_t *boards, int n, int *out_len, uint8_t *out_moves,
                          uint64_t *out_nodes_per_iter, void *stream);
@@ -280,9 +301,12 @@ void bpida_server_set_time_slice(bpida_server *sv, int microseconds);
 /* Stop the service (pending requests are dropped) and free it. */
 void bpida_server_destroy(bpida_server *sv);
 
-/* Statistics of the last solve call made by this host thread. If `timed` is
- * set before a call (bpida_set_timing(1)), search kernel durations are
- * recorded with CUDA events on the launching stream. */
+/* Statistics of the last solve call made by this host thread, complete once
+ * that call's stream has been synchronised (the loop counts of a
+ * graph-driven call are copied back at its end; they are zero if the
+ * workspace it used has served a later call since). If timing is on before
+ * a call (bpida_set_timing(1)), search kernel durations are recorded with
+ * CUDA events on the launching stream (driver = 1 only). */
 void bpida_set_timing(int on);
 void bpida_get_stats(bpida_stats *out);
 
@@ -325,9 +349,9 @@ typedef struct bpida_pdb bpida_pdb;
  * owns the tables until bpida_pdb_destroy. Errors: BPIDA_EINVAL (bad
  * width or grouping), BPIDA_ENOMEM, BPIDA_ECUDA. */
 bpida_status bpida_pdb_create(int width, const int *group_of_tile, bpida_pdb **out, void *stream);
-/* Frees the tables (on the device they were built on). Solve calls return
- * after their results are written, so this is safe once no other host
- * thread is inside a call that uses `pdb`. */
+/* Frees the tables (on the device they were built on), after waiting for the
+ * device's work to finish (a solve call that reads them may still be
+ * running on some stream). No call that uses `pdb` may be issued after. */
 void bpida_pdb_destroy(bpida_pdb *pdb);
 int bpida_pdb_groups(const bpida_pdb *pdb);
 /* Bytes of group `group`'s table (0 for a bad group) and its largest entry

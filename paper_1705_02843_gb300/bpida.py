@@ -215,6 +215,9 @@ def release_workspace() -> None:
 
 @dataclass
 class Solution:
+    """The outputs of one solve call. The call is asynchronous: ``status`` is
+    whether it was issued, and the tensors hold the results once ``stream``
+    has reached the end of its work (``synchronize()``; ``to_host()`` does)."""
     status: int                    # call status
     length: torch.Tensor           # int32 (n,)
     moves: torch.Tensor            # uint8 (n, max_len)
@@ -222,9 +225,16 @@ class Solution:
     iters: torch.Tensor            # int32 (n,)
     inst_status: torch.Tensor      # int32 (n,)
     solutions: Optional[torch.Tensor] = None  # int64 (n,): optimal solutions (count-all mode)
+    stream: Optional[torch.cuda.Stream] = None  # the stream the call was issued on
+
+    def synchronize(self) -> None:
+        if self.stream is not None:
+            self.stream.synchronize()
 
     def to_host(self):
-        """Per-instance dicts with Python ints (moves trimmed to the length)."""
+        """Per-instance dicts with Python ints (moves trimmed to the length),
+        after waiting for the call's stream."""
+        self.synchronize()
         L = self.length.cpu().tolist()
         mv = self.moves.cpu().numpy()
         nd = self.nodes.cpu().numpy().view("uint64")
@@ -257,9 +267,11 @@ def solve(boards: torch.Tensor, width: int = 4, config: Optional[Config] = None,
 
     ``boards``: CUDA int64 tensor, shape (n,) for width 3/4, (n, 2) for 5,
     holding the packed words (bit pattern of the uint64 layout in bpida.h).
-    Outputs are allocated on the same device; the call runs on ``stream``
-    (default: the current stream). With ``pdb`` the heuristic is that
-    pattern database (bpida_solve_pdb), else the Manhattan distance.
+    Outputs are allocated on the same device; the call is issued on
+    ``stream`` (default: the current stream) and returns without waiting
+    (graph driver): the outputs are valid once that stream has reached the
+    end of the call. With ``pdb`` the heuristic is that pattern database
+    (bpida_solve_pdb), else the Manhattan distance.
     """
     lib = load()
     if not boards.is_cuda:
@@ -288,7 +300,7 @@ def solve(boards: torch.Tensor, width: int = 4, config: Optional[Config] = None,
             rc = lib.bpida_solve_ex(ctypes.byref(cfg), boards.data_ptr(), n, *outs)
         else:
             rc = lib.bpida_solve_pdb(ctypes.byref(cfg), pdb.handle, boards.data_ptr(), n, *outs)
-    return Solution(rc, out_len, out_moves, out_nodes, out_iters, out_status, out_sol)
+    return Solution(rc, out_len, out_moves, out_nodes, out_iters, out_status, out_sol, s)
 
 
 def solve_packed_host(packed, width: int = 4, config: Optional[Config] = None,
@@ -327,7 +339,7 @@ def solve_noalloc(boards: torch.Tensor, stream: Optional[torch.cuda.Stream] = No
         rc = lib.bpida_solve_noalloc(boards.data_ptr(), n, out_len.data_ptr(), out_moves.data_ptr(),
                                      out_nodes.data_ptr(), out_iters.data_ptr(), out_status.data_ptr(),
                                      s.cuda_stream)
-    return Solution(rc, out_len, out_moves, out_nodes, out_iters, out_status)
+    return Solution(rc, out_len, out_moves, out_nodes, out_iters, out_status, None, s)
 
 
 class PatternDb:

@@ -14,9 +14,14 @@
 //
 // By default the whole loop is one CUDA graph: the step loop and the pass
 // loop are conditional WHILE nodes whose conditions are set on the device,
-// so a call is one graph launch and one final synchronisation. The
-// host-driven loop (driver = 1) launches the same kernels one by one and
-// reads the control block back after every pass; it is what times each
+// so a call is two launches enqueued on the caller's stream (the argument
+// block, then the graph) and returns without waiting: calls are
+// stream-ordered and asynchronous. Each call takes a workspace of its own
+// from a small per-device pool: the one last used on the same stream (the
+// stream orders the two calls), else an idle one, else a new one, so calls
+// on different streams run concurrently. The host-driven loop (driver = 1)
+// launches the same kernels one by one and reads the control block back
+// after every pass (it synchronises the stream); it is what times each
 // search launch with CUDA events.
 #include "bpida.h"
 #include "bpida_device.cuh"
@@ -70,8 +75,12 @@ struct Plan {
 
 struct Workspace {
     DevBuf state, act0, act1, ctr, scratch, count, offset, q0, q1, ctrl, desc, ovf, fuse;
-    Ctrl *h_ctrl = nullptr;
+    Ctrl *h_ctrl = nullptr;  // pinned copy of the control block, written at the end of each call
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t done = nullptr;         // recorded after the last call's work
+    cudaStream_t last_stream = nullptr;  // stream of the last call
+    bool used = false;                  // a call has been enqueued with it
+    unsigned long long last_call = 0;
     unsigned gen = 1;  // bumped whenever a buffer moves
     std::map<PlanKey, Plan> plans;
     unsigned long long use_clock = 0;
@@ -81,6 +90,9 @@ struct Workspace {
     static constexpr size_t MAX_PLANS = 8;
     void trim_plans()
     {
+        // a graph may still be running: wait before destroying any
+        if (!plans.empty())
+            wait_idle();
         for (auto it = plans.begin(); it != plans.end();) {
             if (!it->second.exec || it->second.gen != gen) {
                 it->second.destroy();
@@ -99,13 +111,23 @@ struct Workspace {
         }
     }
 
+    // The last call's work has finished (before a buffer is freed).
+    cudaError_t wait_idle()
+    {
+        return used && done ? cudaEventSynchronize(done) : cudaSuccess;
+    }
+
     cudaError_t ensure(DevBuf &b, size_t bytes)
     {
         bytes = std::max<size_t>(bytes, 256);
         if (b.n >= bytes)
             return cudaSuccess;
-        if (b.p)
+        if (b.p) {
+            const cudaError_t e = wait_idle();
+            if (e != cudaSuccess)
+                return e;
             cudaFree(b.p);
+        }
         b.p = nullptr;
         b.n = 0;
         ++gen;
@@ -116,6 +138,7 @@ struct Workspace {
     }
     void release()
     {
+        wait_idle();
         for (auto &kv : plans)
             kv.second.destroy();
         plans.clear();
@@ -135,19 +158,70 @@ struct Workspace {
             cudaEventDestroy(ev0);
         if (ev1)
             cudaEventDestroy(ev1);
-        ev0 = ev1 = nullptr;
+        if (done)
+            cudaEventDestroy(done);
+        ev0 = ev1 = done = nullptr;
+        used = false;
+        last_stream = nullptr;
     }
 };
 
-std::vector<Workspace *> g_ws;
+// Per device, a pool of at most MAX_WORKSPACES workspaces.
+constexpr size_t MAX_WORKSPACES = 4;
+std::vector<std::vector<Workspace *>> g_ws;
+unsigned long long g_calls = 0;
 
-Workspace *workspace_for(int dev)
+// The workspace for a call on stream st (under g_mu): the one whose last
+// call was on st (the stream orders the two calls), else an idle one, else a
+// new one while the pool is small, else the least recently used one, with st
+// made to wait (on the device) for that workspace's last call.
+Workspace *workspace_for(int dev, cudaStream_t st, cudaError_t *err)
 {
+    *err = cudaSuccess;
     if ((int)g_ws.size() <= dev)
-        g_ws.resize(dev + 1, nullptr);
-    if (!g_ws[dev])
-        g_ws[dev] = new Workspace();
-    return g_ws[dev];
+        g_ws.resize(dev + 1);
+    std::vector<Workspace *> &pool = g_ws[dev];
+    for (Workspace *w : pool)
+        if (w->used && w->last_stream == st)
+            return w;
+    for (Workspace *w : pool)
+        if (!w->used || cudaEventQuery(w->done) == cudaSuccess)
+            return w;
+    cudaGetLastError();  // cudaEventQuery's cudaErrorNotReady is not an error of this call
+    if (pool.size() < MAX_WORKSPACES) {
+        pool.push_back(new Workspace());
+        return pool.back();
+    }
+    Workspace *lru = pool[0];
+    for (Workspace *w : pool)
+        if (w->last_call < lru->last_call)
+            lru = w;
+    *err = cudaStreamWaitEvent(st, lru->done, 0);
+    return lru;
+}
+
+// The calling thread's last graph-driven call: its workspace, whose pinned
+// control block receives the call's loop state at the end of the call, and
+// the call's number (the workspace may have served a later call since).
+struct LastCall {
+    Workspace *ws = nullptr;
+    unsigned long long call = 0;
+};
+thread_local LastCall g_last;
+
+// The statistics that come from the control block of a finished call.
+void fill_loop_stats(bpida_stats &s, const Ctrl &c, bool graph)
+{
+    s.steps = c.steps;
+    s.passes = (int)c.passes_total;
+    s.records = c.records_total;
+    s.handed_back = c.handed_back_total;
+    s.search_nodes = c.search_nodes_total;
+    s.spills = c.spills;
+    s.max_handed_back = c.max_out;
+    s.search_ms_device = (double)c.search_ns * 1e-6;
+    if (graph)  // k_set_desc, k_init, k_finalize; k_split and k_advance per step; k_search per pass
+        s.launches = 3 + 2 * c.steps + (int)c.passes_total;
 }
 
 struct Settings {
@@ -281,7 +355,9 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
 {
     int dev = 0;
     CK(cudaGetDevice(&dev));
-    Workspace &ws = *workspace_for(dev);
+    cudaError_t wse = cudaSuccess;
+    Workspace &ws = *workspace_for(dev, st, &wse);
+    CK(wse);
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
 
@@ -349,6 +425,7 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     if (!ws.ev0) {
         CK(cudaEventCreate(&ws.ev0));
         CK(cudaEventCreate(&ws.ev1));
+        CK(cudaEventCreateWithFlags(&ws.done, cudaEventDisableTiming));
     }
 
     Dev<W> d;
@@ -454,63 +531,70 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
         Plan &pl = found->second;
         pl.last_use = ++ws.use_clock;
         CK(cudaGraphLaunch(pl.exec, st));
+        // the loop state goes to the pinned copy at the end of the call;
+        // bpida_get_stats reads it once the caller has synchronised
         CK(cudaMemcpyAsync(ws.h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        stats.launches = 3 + 2 * ws.h_ctrl->steps + (int)ws.h_ctrl->passes_total;
-    } else {
-        // host-driven loop over the same kernels
-        d.graph = 0;
-        k_init<W, PDB><<<g_inst, b128, 0, st>>>(d);
+        CK(cudaEventRecord(ws.done, st));
+        ws.used = true;
+        ws.last_stream = st;
+        ws.last_call = ++g_calls;
+        g_stats = stats;
+        g_last.ws = &ws;
+        g_last.call = ws.last_call;
+        // problems the device finds (queue capacity, a failed internal check)
+        // are reported per instance by k_finalize
+        return BPIDA_OK;
+    }
+    // host-driven loop over the same kernels (synchronous)
+    d.graph = 0;
+    k_init<W, PDB><<<g_inst, b128, 0, st>>>(d);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ws.h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    stats.launches = 2;
+    int n_active = ws.h_ctrl->n_active;
+    while (n_active > 0) {
+        k_split<W, PDB><<<n_active, bsplit, 0, st>>>(d);
         CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(ws.h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        stats.launches = 2;
-        int n_active = ws.h_ctrl->n_active;
-        while (n_active > 0) {
-            k_split<W, PDB><<<n_active, bsplit, 0, st>>>(d);
+        stats.launches += 1;
+        for (;;) {
+            if (g_timing)
+                CK(cudaEventRecord(ws.ev0, st));
+            search_kernel<W, S, PDB>(cfg.variant, fuse)<<<g.grid, g.threads, g.smem, st>>>(d);
             CK(cudaGetLastError());
-            stats.launches += 1;
-            for (;;) {
-                if (g_timing)
-                    CK(cudaEventRecord(ws.ev0, st));
-                search_kernel<W, S, PDB>(cfg.variant, fuse)<<<g.grid, g.threads, g.smem, st>>>(d);
-                CK(cudaGetLastError());
-                if (g_timing)
-                    CK(cudaEventRecord(ws.ev1, st));
-                stats.launches += 1;
-                CK(cudaMemcpyAsync(ws.h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-                CK(cudaStreamSynchronize(st));
-                if (g_timing) {
-                    float ms = 0.f;
-                    CK(cudaEventElapsedTime(&ms, ws.ev0, ws.ev1));
-                    stats.search_ms += ms;
-                }
-                if (!ws.h_ctrl->pass_again)
-                    break;
-            }
-            k_advance<W><<<(n_active + 127) / 128, b128, 0, st>>>(d);
-            CK(cudaGetLastError());
+            if (g_timing)
+                CK(cudaEventRecord(ws.ev1, st));
             stats.launches += 1;
             CK(cudaMemcpyAsync(ws.h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
-            n_active = ws.h_ctrl->step_again ? ws.h_ctrl->n_active : 0;
+            if (g_timing) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, ws.ev0, ws.ev1));
+                stats.search_ms += ms;
+            }
+            if (!ws.h_ctrl->pass_again)
+                break;
         }
-        k_finalize<W><<<g_inst, b128, 0, st>>>(d);
+        k_advance<W><<<(n_active + 127) / 128, b128, 0, st>>>(d);
         CK(cudaGetLastError());
         stats.launches += 1;
         CK(cudaMemcpyAsync(ws.h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        n_active = ws.h_ctrl->step_again ? ws.h_ctrl->n_active : 0;
     }
-    const Ctrl &c = *ws.h_ctrl;
-    stats.steps = c.steps;
-    stats.passes = (int)c.passes_total;
-    stats.records = c.records_total;
-    stats.handed_back = c.handed_back_total;
-    stats.search_nodes = c.search_nodes_total;
-    stats.spills = c.spills;
-    stats.max_handed_back = c.max_out;
-    stats.search_ms_device = (double)c.search_ns * 1e-6;
+    k_finalize<W><<<g_inst, b128, 0, st>>>(d);
+    CK(cudaGetLastError());
+    stats.launches += 1;
+    CK(cudaMemcpyAsync(ws.h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(ws.done, st));
+    ws.used = true;
+    ws.last_stream = st;
+    ws.last_call = ++g_calls;
+    CK(cudaStreamSynchronize(st));
+    fill_loop_stats(stats, *ws.h_ctrl, false);
     g_stats = stats;
+    g_last.ws = nullptr;
+    const Ctrl &c = *ws.h_ctrl;
     if (c.err & ERR_QUEUE)
         return BPIDA_ENOMEM;
     if (c.err)
@@ -712,8 +796,15 @@ void bpida_set_fuse_nodes(uint64_t nodes) { g_fuse_nodes.store(nodes); }
 
 void bpida_get_stats(bpida_stats *out)
 {
-    if (out)
-        *out = g_stats;
+    if (!out)
+        return;
+    bpida_stats s = g_stats;
+    if (g_last.ws) {
+        std::lock_guard<std::mutex> lock(g_mu);
+        if (g_last.ws->last_call == g_last.call && g_last.ws->h_ctrl)
+            fill_loop_stats(s, *g_last.ws->h_ctrl, true);
+    }
+    *out = s;
 }
 
 void bpida_release_workspace(void)
@@ -722,8 +813,10 @@ void bpida_release_workspace(void)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess)
         return;
-    if (dev < (int)g_ws.size() && g_ws[dev])
-        g_ws[dev]->release();
+    if (dev < (int)g_ws.size())
+        for (Workspace *w : g_ws[dev])
+            w->release();
+    g_last.ws = nullptr;
     tp::release(dev);
 }
 

@@ -236,6 +236,8 @@ void bpida_pdb_destroy(bpida_pdb *pdb)
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(pdb->dev);
+    // solve calls are asynchronous: one that reads the tables may still run
+    cudaDeviceSynchronize();
     cudaFree(pdb->tab);
     cudaFree(pdb->d_info);
     cudaSetDevice(cur);
