@@ -95,7 +95,8 @@ typedef struct {
     int split_target;     /* max frontier records per instance; 0 = auto */
     int warps_per_block;  /* search kernel block size in warps; 0 = auto */
     int stack_entries;    /* per-warp shared-memory stack, 0 = auto
-                             (one of 256, 384, 480, 512, 768, 1024) */
+                             (480 for width 4, else 512); one of 256,
+                             384, 480, 512, 768, 1024 */
     int exit_fraction_pct;/* percentage of warps that must have run out of
                              work before busy warps hand their stacks back
                              for redistribution; 0 = auto */

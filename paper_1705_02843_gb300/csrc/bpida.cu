@@ -371,7 +371,7 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     const int wpb = cfg.variant == 1 ? 1 : cfg.wpb;  // the paper's kernel: block = warp
     g.threads = wpb * 32;
     // search stack entries: 16 bytes, 24 for W = 5 and the pattern-database search
-    g.smem = SharedLut<W>::BYTES + (size_t)wpb * S * WarpStack<W, (W == 5) || PDB>::ENTRY_BYTES;
+    g.smem = SearchSmem<W, PDB>::TABLES + (size_t)wpb * S * WarpStack<W, (W == 5) || PDB>::ENTRY_BYTES;
     // one kernel serves every block size (and the serving path), so its
     // dynamic shared memory limit is set once to the device's maximum; the
     // blocks per SM are looked up once per (device, block size, kernel)
@@ -666,7 +666,9 @@ bpida_status parse_settings(const bpida_config *cfg_in, int n, Settings &cfg)
     cfg.count_all = cfg_in ? cfg_in->count_all : 1;
     cfg.split_target = cfg_in ? cfg_in->split_target : 0;
     cfg.wpb = (cfg_in && cfg_in->warps_per_block > 0) ? cfg_in->warps_per_block : 4;
-    cfg.S = (cfg_in && cfg_in->stack_entries > 0) ? cfg_in->stack_entries : 512;
+    // 15-puzzle: 480 entries keep seven 4-warp search blocks per SM (more
+    // resident warps outweigh the extra stack spills); otherwise 512
+    cfg.S = (cfg_in && cfg_in->stack_entries > 0) ? cfg_in->stack_entries : (cfg.width == 4 ? 480 : 512);
     cfg.exit_pct = (cfg_in && cfg_in->exit_fraction_pct > 0) ? cfg_in->exit_fraction_pct : 10;
     cfg.min_rounds = (cfg_in && cfg_in->min_rounds > 0) ? cfg_in->min_rounds : 64;
     cfg.driver = cfg_in ? cfg_in->driver : 0;

@@ -536,6 +536,83 @@ template <int W> __device__ __forceinline__ uint32_t rec_from_sm(uint32_t m)
     return m_make((m & 127u) / (uint32_t)Geo<W>::BITS, last, (m >> 11) & 255u);
 }
 
+// ---- the 15-puzzle search step, four moves at once ----
+// With the Manhattan distance on the 4x4 board, the four candidate moves of
+// a node are handled together: their neighbour tiles are gathered into the
+// four bytes of one word (byte m: move m, in the order up, left, right,
+// down), and whether each tile slides away from its goal cell is one packed
+// comparison against per-position thresholds:
+//   up    (tile from row r-1 to r): away iff t < 4r
+//   left  (tile from col c-1 to c): away iff (t & 3) < c
+//   right (tile from col c+1 to c): away iff 3 - (t & 3) < 3 - c
+//   down  (tile from row r+1 to r): away iff 15 - t < 12 - 4r
+// Each byte holds x = the tile term (at most 15) and the per-position table
+// holds a + 127 (a = the threshold, at most 15), so (a + 127 - x) sets bit 7
+// of its byte exactly when x < a and never borrows from the next byte.
+// The search stack's metadata for this step sets bit 8m + 7 when move m is
+// the inverse of the parent's move (it is excluded), keeps the blank's
+// position in bits 0..3 and the slack in bits 8..14 (slack <= 80: the
+// longest limit).
+template <int W, bool PDB> struct FourMoves {
+    static constexpr bool on = W == 4 && !PDB;
+};
+static constexpr uint32_t FM_BIT7 = 0x80808080u;
+__device__ __forceinline__ uint32_t fm_from_rec(uint32_t m)
+{
+    const uint32_t last = m_last(m);
+    const uint32_t excl = last < 4u ? (0x80u << (8u * (3u - last))) : 0u;
+    return m_blank(m) | ((uint32_t)m_slack(m) << 8) | excl;
+}
+__device__ __forceinline__ uint32_t rec_from_fm(uint32_t m)
+{
+    const uint32_t e = m & FM_BIT7;
+    const uint32_t last = e ? 3u - (uint32_t)((__ffs((int)e) - 1) >> 3) : LAST_NONE;
+    return m_make(m & 15u, last, (m >> 8) & 127u);
+}
+// Per blank position p, in shared memory: entry p (16 bytes)
+//   x: byte selector of the neighbours (up, left, right, down) in the board
+//      viewed as 8 bytes (an off-board neighbour selects byte 0)
+//   y: 0x0F in byte m when neighbour m's tile is the low nibble of its byte
+//   z: per byte m, 127 + the threshold of move m
+//   w: bit 8m + 7 set when move m keeps the blank on the board
+// and entries 16 + 2p, 17 + 2p: per move m, the low and high 32 bits of
+// 16^p + 16^(p + displacement of m) (0 for a move off the board).
+struct FourMoveTable {
+    static constexpr int BYTES = 16 * 16 + 16 * 32;
+    __device__ static void load(uint4 *t)
+    {
+        for (int p = threadIdx.x; p < 16; p += blockDim.x) {
+            const int r = p >> 2, c = p & 3;
+            const int np[4] = {p - 4, p - 1, p + 1, p + 4};
+            const bool on[4] = {r > 0, c > 0, c < 3, r < 3};
+            const int thr[4] = {4 * r, c, 3 - c, 12 - 4 * r};
+            uint32_t sel = 0, lowm = 0, z = 0, legal = 0;
+            for (int m = 0; m < 4; ++m) {
+                const int q = on[m] ? np[m] : 0;
+                sel |= (uint32_t)(q >> 1) << (4 * m);
+                if ((q & 1) == 0)
+                    lowm |= 0x0Fu << (8 * m);
+                z |= (uint32_t)(127 + thr[m]) << (8 * m);
+                if (on[m])
+                    legal |= 0x80u << (8 * m);
+            }
+            t[p] = make_uint4(sel, lowm, z, legal);
+            uint32_t lo[4], hi[4];
+            for (int m = 0; m < 4; ++m) {
+                const uint64_t v = on[m] ? (1ull << (4 * p)) | (1ull << (4 * np[m])) : 0ull;
+                lo[m] = (uint32_t)v;
+                hi[m] = (uint32_t)(v >> 32);
+            }
+            t[16 + 2 * p] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            t[17 + 2 * p] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        }
+    }
+};
+// Shared memory of the search kernel before the warp stacks.
+template <int W, bool PDB = false> struct SearchSmem {
+    static constexpr int TABLES = SharedLut<W>::BYTES + (FourMoves<W, PDB>::on ? FourMoveTable::BYTES : 0);
+};
+
 // W <= 4: one 16-byte entry {board lo, board hi, meta, origin}.
 // W == 5, and the pattern-database search: a 16-byte board array (the
 // 128-bit board; slot board and inverse board) and an 8-byte {meta, origin}
@@ -664,7 +741,7 @@ template <int W> __device__ __forceinline__ LutRow<W> lut_row_sh(const unsigned 
 template <int W, int S, bool PDB = false, typename Stack = WarpStack<W>>
 __device__ __forceinline__ void hand_back_stack(const Dev<W> &a, Rec<W> *out, const Stack &stk,
                                                 int from, int k, unsigned inst, int lane,
-                                                const PdbInfo *pi = nullptr)
+                                                const PdbInfo *pi = nullptr, bool fm = false)
 {
     if (k <= 0)
         return;
@@ -686,7 +763,7 @@ __device__ __forceinline__ void hand_back_stack(const Dev<W> &a, Rec<W> *out, co
             r.b = pdb_board<W>((uint64_t)(b >> 64), *pi);
         else
             r.b = b;
-        r.meta = rec_from_sm<W>(m);
+        r.meta = fm ? rec_from_fm(m) : rec_from_sm<W>(m);
         r.inst = inst;
         r.origin = o;
         r.pm = 0;
@@ -777,6 +854,7 @@ __global__ void k_search(const Dev<W> a)
     typedef SearchBoard<W, PDB> SB;  // what a stack entry holds (B, or the PDB pair)
     typedef WarpStack<W, (W == 5) || PDB> Stack;
     constexpr int BITS = Geo<W>::BITS;
+    constexpr bool FM = FourMoves<W, PDB>::on;           // four moves at once (15-puzzle)
     extern __shared__ __align__(16) unsigned char smem[];
     // end-of-pass bookkeeping is combined per block, so that the grid-wide
     // counters see one atomic per block instead of one per warp
@@ -791,6 +869,8 @@ __global__ void k_search(const Dev<W> a)
         s_nodes = 0;
     }
     SharedLut<W>::load(lut, a.lut);
+    if constexpr (FourMoves<W, PDB>::on)
+        FourMoveTable::load((uint4 *)(smem + SharedLut<W>::BYTES));
     const PdbInfo *pi = nullptr;
     if constexpr (PDB) {
         static_assert(W <= 4, "pattern databases: 8- and 15-puzzle");
@@ -809,7 +889,17 @@ __global__ void k_search(const Dev<W> a)
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Stack stk;
-    stk.init(smem + SharedLut<W>::BYTES + (size_t)warp * S * Stack::ENTRY_BYTES, S);
+    stk.init(smem + SearchSmem<W, PDB>::TABLES + (size_t)warp * S * Stack::ENTRY_BYTES, S);
+    const uint4 *fmtab = (const uint4 *)(smem + SharedLut<W>::BYTES);
+    // byte selectors and the slack step of the four-move children, read
+    // from shared memory so that they stay multiplier operands
+    __shared__ uint32_t s_one;
+    if (threadIdx.x == 0)
+        s_one = 1u;
+    __syncthreads();
+    const uint32_t one = *(volatile uint32_t *)&s_one;
+    const uint32_t ebyte[4] = {one, one << 8, one << 16, one << 24};
+    const uint32_t neg4 = 0u - 4u * one;
     // this warp's overflow stack in global memory: the oldest open nodes go
     // there when the shared stack is full and come back when it drains
     // (24-puzzle only: its deeper trees overflow the shared stack often)
@@ -832,6 +922,10 @@ __global__ void k_search(const Dev<W> a)
     unsigned acc_inst = 0xffffffffu;
     unsigned long long acc_nodes = 0, tot_nodes = 0;
     int fmin = INT_MAX;
+    // four-move step: bit 7 of a byte is set once a child was pruned; the
+    // slack is even (f keeps the parity of h(start), and limits rise by 2),
+    // so a node with slack < 2 has slack 0 and its pruned children f = limit + 2
+    uint32_t prn = 0;
     // fused iterations: nodes popped with slack 2m (m < acc_J) of acc_inst,
     // counted by lane 0 in shared memory
     int acc_J = 0;
@@ -840,6 +934,9 @@ __global__ void k_search(const Dev<W> a)
         for (int m = 0; m < FUSE_MAX; ++m)
             lowc[m] = 0;
     auto publish = [&]() {
+        if (FM && prn)
+            fmin = min(fmin, 2);
+        prn = 0;
         const int fm = warp_min_int(fmin);
         if (lane == 0 && acc_inst != 0xffffffffu) {
             if (acc_nodes)
@@ -889,7 +986,7 @@ __global__ void k_search(const Dev<W> a)
                     pdb_h(a.pdb, *pi, (uint64_t)(e >> 64), &vb);
                     stk.put(lane, e, sm_from_rec<W>(r.meta) | vb, r.origin);
                 } else {
-                    stk.put(lane, r.b, sm_from_rec<W>(r.meta), r.origin);
+                    stk.put(lane, r.b, FM ? fm_from_rec(r.meta) : sm_from_rec<W>(r.meta), r.origin);
                 }
             }
             int top = dropped ? 0 : cnt;
@@ -922,7 +1019,7 @@ __global__ void k_search(const Dev<W> a)
                     // four): move the oldest entries to the overflow stack,
                     // or hand them to the next pass when it is full, and move
                     // the rest down. Afterwards top <= max(n, S/2), so
-                    // top + 3n <= S for S >= 256.
+                    // top + 3n <= S for S >= 192 KN.
                     const int k = min(top - n, S / 2);
                     if (lane == 0)
                         atomicAdd(&a.ctrl->spills, 1ull);
@@ -935,7 +1032,7 @@ __global__ void k_search(const Dev<W> a)
                         }
                         ovf_n += k;
                     } else {
-                        hand_back_stack<W, S, PDB>(a, out, stk, 0, k, inst0, lane, pi);
+                        hand_back_stack<W, S, PDB>(a, out, stk, 0, k, inst0, lane, pi, FM);
                     }
                     __syncwarp();
                     for (int j0 = 0; j0 < top - k; j0 += 32) {
@@ -952,6 +1049,7 @@ __global__ void k_search(const Dev<W> a)
                     }
                     top -= k;
                 }
+                // pop: lane l takes entry top - n + l
                 const bool act = lane < n;
                 SB b = 0;
                 uint32_t mt = 0, org = 0;
@@ -973,15 +1071,15 @@ __global__ void k_search(const Dev<W> a)
                     }
                     if (FUSE && J && goal) {
                         // a goal at slack s belongs to iteration J - s/2 of the step
-                        const int j = J - (int)((mt >> 12) & 127u);
+                        const int j = J - (int)(FM ? (mt >> 9) & 63u : (mt >> 12) & 127u);
                         if (j >= 0) {
                             atomicAdd(&a.fuse.goals[(size_t)inst0 * FUSE_K + j], 1ull);
                             atomicMin(&a.fuse.origin[(size_t)inst0 * FUSE_K + j], org);
                         }
                     }
                 }
-                const uint32_t sh_p = mt & 127u;
-                const int s = (int)((mt >> 11) & 255u);
+                int base = top;
+                const int s = FM ? (int)((mt >> 8) & 127u) : (int)((mt >> 11) & 255u);
                 if (FUSE && J) {
                     // popped nodes above the lower limits of the step
                     for (int m = 0; m < J; ++m) {
@@ -990,11 +1088,61 @@ __global__ void k_search(const Dev<W> a)
                             lowc[m] += c;
                     }
                 }
-                const unsigned allowed = (act && !goal) ? (LegalMoves<W>::at_sh(sh_p) & ~((mt >> 7) & 15u)) : 0u;
+                if constexpr (FM) {
+                    // the four moves at once (see FourMoves)
+                    const uint32_t mq = mt;
+                    const uint4 e = fmtab[mq & 15u];
+                    const uint64_t bq = (uint64_t)b;
+                    const uint32_t G = __byte_perm((uint32_t)bq, (uint32_t)(bq >> 32), e.x);
+                    // byte m's low nibble: the tile that move m slides into the blank
+                    const uint32_t Y = (G & e.y) | ((G >> 4) & ~e.y);
+                    const uint32_t X = (Y & 0x0F03030Fu) ^ 0x0F030000u;
+                    const uint32_t away4 = (e.z - X) & FM_BIT7;
+                    const uint32_t allowed4 = (act && !goal) ? (e.w & ~mq) : 0u;
+                    const uint32_t low4 = (mq & 0x7E00u) ? 0u : FM_BIT7;  // slack < 2
+                    const uint32_t push4 = allowed4 & ~(away4 & low4);
+                    prn |= allowed4 & away4 & low4;
+                    const uint32_t sh_p = (mq & 15u) << 2;
+                    const uint32_t keep = mq & 0x7F0Fu;  // blank position and slack
+                    // slots: this lane's children go to sp, sp + 1, ... (the
+                    // prefix of the per-lane counts, from their bit-sliced ballots)
+                    const unsigned c = __popc(push4);
+                    const unsigned B0 = __ballot_sync(FULL, c & 1u), B1 = __ballot_sync(FULL, c & 2u),
+                                   B2 = __ballot_sync(FULL, c & 4u);
+                    int sp = base + __popc(B0 & lt) + 2 * __popc(B1 & lt) + 4 * __popc(B2 & lt);
+                    base += __popc(B0) + 2 * __popc(B1) + 4 * __popc(B2);
+                    // the children: move m XORs its tile t into the blank's field and
+                    // the neighbour's field, i.e. adds t times a per-position
+                    // constant to each 32-bit half (the fields never carry); the
+                    // tile and the away bit of byte m are read with byte dot
+                    // products, so the step's arithmetic runs on the multiply-add
+                    // pipe rather than on the integer ALU pipe, which the tests
+                    // and the bit logic above already keep busy
+                    const uint32_t Yc = Y & 0x0F0F0F0Fu;
+                    const uint4 ml = fmtab[16 + (mq & 15u) * 2], mh = fmtab[17 + (mq & 15u) * 2];
+                    const uint32_t mlo[4] = {ml.x, ml.y, ml.z, ml.w}, mhi[4] = {mh.x, mh.y, mh.z, mh.w};
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const uint32_t t = (uint32_t)__dp4a(Yc, ebyte[m], 0u);
+                        const uint32_t clo = (uint32_t)bq ^ (t * mlo[m]), chi = (uint32_t)(bq >> 32) ^ (t * mhi[m]);
+                        const B child = ((uint64_t)chi << 32) | clo;
+                        // the child's blank, its excluded move (the inverse of m)
+                        // and its slack (s - 2 when the tile moved away, else s)
+                        const uint32_t aw = (uint32_t)__dp4a(away4, ebyte[m], 0u);  // 128 when away
+                        const uint32_t cm = aw * neg4 + (keep + (uint32_t)move_off<W>(m) + (0x80u << (8 * (3 - m))));
+                        if (push4 & (0x80u << (8 * m))) {
+                            stk.put(sp, child, cm, org);
+                            ++sp;
+                        }
+                    }
+
+                } else {
+                const uint32_t sh_p = mt & 127u;
+                const unsigned allowed =
+                    (act && !goal) ? (LegalMoves<W>::at_sh(sh_p) & ~((mt >> 7) & 15u)) : 0u;
                 const bool low = s < 2;
                 const uint32_t sbase = mt & (255u << 11);
                 bool pruned = false;
-                int base = top;
                 if constexpr (PDB) {
                     // b holds the inverse board (high half) and the slot board
                     // (low half); the step's direction comes from the moved
@@ -1064,9 +1212,10 @@ __global__ void k_search(const Dev<W> a)
                     base += __popc(pm);
                 }
                 }
-                top = base;
                 if (pruned)
                     fmin = min(fmin, 2 - s);
+                }
+                top = base;
                 __syncwarp();
 
                 if (((++rounds) & 31) == 0) {
@@ -1120,9 +1269,9 @@ __global__ void k_search(const Dev<W> a)
             if (budgeted)
                 publish();
             if (stop) {
-                hand_back_stack<W, S, PDB>(a, out, stk, 0, top, inst0, lane, pi);
+                hand_back_stack<W, S, PDB>(a, out, stk, 0, top, inst0, lane, pi, FM);
                 if (OVF)
-                    hand_back_stack<W, S, PDB>(a, out, ovf, 0, ovf_n, inst0, lane, pi);
+                    hand_back_stack<W, S, PDB>(a, out, ovf, 0, ovf_n, inst0, lane, pi, FM);
                 ovf_n = 0;
                 hand_back_records<W>(a, frontier, n_act, n_front, act, in, out, i + cnt, end, lane);
                 // input that no warp has taken yet goes back too (a stop at

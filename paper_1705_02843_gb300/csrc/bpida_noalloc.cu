@@ -138,7 +138,7 @@ extern "C" bpida_status bpida_solve_noalloc(const uint64_t *boards, int n, int *
     }
     const int grid = sms;
     const int threads = NA_WPB * 32;
-    const size_t smem = SharedLut<4>::BYTES + (size_t)NA_WPB * NA_S * WarpStack<4>::ENTRY_BYTES;
+    const size_t smem = SearchSmem<4>::TABLES + (size_t)NA_WPB * NA_S * WarpStack<4>::ENTRY_BYTES;
     d.tune.min_rounds = 64;
     d.tune.exit_threshold = (grid * NA_WPB) / 10 > 0 ? (grid * NA_WPB) / 10 : 1;
     d.tune.nodes_per_record = 4096;

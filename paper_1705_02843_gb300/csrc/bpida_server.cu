@@ -35,7 +35,7 @@ using namespace bp;
 namespace {
 
 constexpr int SV_W = 4;
-constexpr int SV_S = 512;
+constexpr int SV_S = 480;
 constexpr int SV_WPB = 4;
 constexpr int SV_MAXLEN = Geo<SV_W>::MAXLEN;
 constexpr int SV_MAXIT = Geo<SV_W>::MAXIT;
@@ -287,7 +287,7 @@ bpida_server *bpida_server_create(const bpida_config *cfg, size_t frontier_bytes
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sv->dev);
     sv->max_slots = slots;
     sv->threads = SV_WPB * 32;
-    sv->smem = SharedLut<SV_W>::BYTES + (size_t)SV_WPB * SV_S * WarpStack<SV_W>::ENTRY_BYTES;
+    sv->smem = SearchSmem<SV_W>::TABLES + (size_t)SV_WPB * SV_S * WarpStack<SV_W>::ENTRY_BYTES;
     int bpsm = 0, smem_max = 0;
     // the device maximum, as the solve path sets it: the kernel is shared
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, sv->dev);
