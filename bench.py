@@ -244,9 +244,14 @@ def run_serving(args):
 
 
 def run_ablation(args):
-    """The paper's BPIDA* kernel (block = warp, 8 nodes x 4 actions per pop,
-    static root assignment, no dynamic load balancing) against this design,
-    on the same workloads and drivers; every result checked equal."""
+    """The paper's BPIDA* against this design, on the same workloads, every
+    result checked equal: the paper's kernel (block = warp, 8 nodes x 4
+    actions per pop, static root shares, no dynamic load balancing) on this
+    design's per-iteration root sets (variant 1, also with 16x wider root
+    sets), and with the paper's own static load balancing (variant 5: a
+    persistent root set split and reassigned after every iteration by the
+    repetitions each root took; one board per run, as in the paper). The
+    4096-board mix is measured on its first --ablation-mix-boards boards."""
     import torch
 
     from paper_1705_02843_gb300 import bpida
@@ -255,20 +260,22 @@ def run_ablation(args):
     out = {}
     for wl in ("perms15_100", "mixed15_4096"):
         insts = I.WORKLOADS[wl]()
+        if wl == "mixed15_4096":
+            insts = insts[:args.ablation_mix_boards]
         b = torch.from_numpy(I.packed_array(insts).view(np.int64)).cuda()
         res = {}
         wide = 65536 if wl == "perms15_100" else 512
-        runs = [("this_design", 0, 0), ("paper_kernel_wide_roots", 1, wide)]
-        if wl == "perms15_100":
-            runs.append(("paper_kernel", 1, 0))
-        for name, variant, split in runs:
+        runs = [("this_design", 0, 0, ("batched", "plain")), ("paper_kernel", 1, 0, ("batched", "plain")),
+                ("paper_kernel_wide_roots", 1, wide, ("batched",)),
+                ("paper_bpida_static_lb", bpida.BPSTATIC, 0, ("plain",))]
+        for name, variant, split, forms in runs:
             cfg = bpida.make_config(4, variant=variant, split_target=split)
-            forms = ("batched", "plain") if wl == "perms15_100" else ("batched",)
             for form in forms:
                 for rep in range(2 if variant == 0 else 1):
                     torch.cuda.synchronize()
                     t0 = time.perf_counter()
-                    if form == "batched":
+                    if form == "batched" or variant >= bpida.PSIMPLE:
+                        # variants 2-5 solve the boards of a call one at a time
                         sols = [bpida.solve(b, 4, cfg)]
                     else:
                         sols = [bpida.solve(b[i:i + 1], 4, cfg) for i in range(len(insts))]
@@ -276,25 +283,22 @@ def run_ablation(args):
                     dt = time.perf_counter() - t0
                 hosts = [h for s in sols for h in s.to_host()]
                 nodes = sum(sum(h["nodes"]) for h in hosts)
-                res[(name, form)] = (dt, nodes, [(h["length"], h["nodes"], h["moves"]) for h in hosts])
-        for form in ("batched", "plain"):
-            if ("this_design", form) not in res:
-                continue
-            a, q = res[("this_design", form)], res[("paper_kernel_wide_roots", form)]
-            p = res.get(("paper_kernel", form))
-            if a[2] != q[2] or (p is not None and a[2] != p[2]):
-                raise RuntimeError("kernels disagree on " + wl)
-            row = {"this_design_expansions_per_s": a[1] / a[0],
-                   "this_design_instances_per_s": len(insts) / a[0],
-                   "paper_kernel_wide_roots_expansions_per_s": q[1] / q[0],
-                   "paper_kernel_wide_roots_instances_per_s": len(insts) / q[0],
-                   "wide_roots_per_instance_cap": wide, "speedup_vs_wide_roots": q[0] / a[0]}
-            if p is not None:
-                row.update({"paper_kernel_expansions_per_s": p[1] / p[0],
-                            "paper_kernel_instances_per_s": len(insts) / p[0], "speedup_vs_paper_kernel": p[0] / a[0]})
-            out["%s_%s" % (wl, form)] = row
-        print(json.dumps({wl: {k: v for k, v in out.items() if k.startswith(wl)}}), file=sys.stderr, flush=True)
-    print(json.dumps({"metric": "ablation: this design vs the paper's BPIDA* kernel (same driver, exact results)",
+                st = bpida.last_stats()
+                res[(name, form)] = (dt, nodes, [(h["length"], h["nodes"], h["moves"]) for h in hosts], st)
+        ref = res[("this_design", "batched")][2]
+        row = {"boards": len(insts)}
+        for (name, form), (dt, nodes, rows, st) in res.items():
+            if rows != ref:
+                raise RuntimeError("%s (%s) disagrees with this design on %s" % (name, form, wl))
+            row["%s_%s" % (name, form)] = {"seconds": dt, "expansions_per_s": nodes / dt,
+                                            "instances_per_s": len(insts) / dt}
+            if name == "paper_bpida_static_lb":
+                row["%s_%s" % (name, form)].update({"search_warps": st["tp_threads"], "final_roots": st["tp_roots"],
+                                                    "lb_ratio_last_board": st["lb_ratio"]})
+        row["wide_roots_per_instance_cap"] = wide
+        out[wl] = row
+        print(json.dumps({wl: row}), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "ablation: this design vs the paper's BPIDA* (same drivers, exact results)",
                       "results": out}), flush=True)
 
 
@@ -1028,6 +1032,8 @@ def main():
                     help="all-solutions node count of the boards the first-solution leg runs on one core")
     ap.add_argument("--ablation", action="store_true",
                     help="compare against the paper's BPIDA* kernel instead")
+    ap.add_argument("--ablation-mix-boards", type=int, default=512,
+                    help="with --ablation: boards of the 4096-board mix to run (its first ones)")
     ap.add_argument("--workloads", action="store_true",
                     help="measure the 4096-board mix (batched and plain) and the 24-puzzle walks instead")
     ap.add_argument("--thread-parallel", action="store_true",

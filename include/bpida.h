@@ -49,7 +49,7 @@
  * call with a new configuration or a larger batch may allocate device
  * memory and build a CUDA graph, and a call that has to grow a busy
  * workspace waits for that workspace's last call first. The host-driven
- * loop (driver = 1), the thread-parallel variants (2-4) and
+ * loop (driver = 1), the ablation variants 2-5 and
  * bpida_solve_noalloc synchronise `stream` before returning. The library
  * serialises its host-side bookkeeping with a process-wide lock, held while
  * a call is enqueued.
@@ -115,8 +115,9 @@ typedef struct {
                              (default); 1 = the paper's BPIDA* kernel
                              (Algorithm 1: block = warp, 8 nodes per pop,
                              lane i applies action i mod 4, roots assigned
-                             statically, no dynamic load balancing), kept as
-                             an ablation; 2, 3, 4 = the paper's thread-
+                             statically, no dynamic load balancing) on this
+                             design's per-iteration root sets, kept as an
+                             ablation; 2, 3, 4 = the paper's thread-
                              parallel configurations PSimple, PStaticLB and
                              PFullLB (Section 4 and its appendix: one
                              sequential depth-first search per thread over
@@ -124,16 +125,22 @@ typedef struct {
                              static rebalancing of a persistent root set by
                              the previous iteration's per-root loads / the
                              same plus idle threads taking untried branches
-                             from busy threads of their block), kept as
-                             ablations. Variants 2-4 take width 3 or 4,
-                             count_all = 1 and no node budget (else
-                             BPIDA_EINVAL), solve the boards one at a time,
-                             use split_target as the number of search
-                             threads (0 = every resident thread) and report
-                             the load balance in bpida_stats; their
-                             solution is an optimal one (for 2 and 3 the
-                             lexicographically first), and every count
-                             equals variant 0's */
+                             from busy threads of their block); 5 = the
+                             paper's BPIDA* with its own static load
+                             balancing (Section 5: variant 1's warp search
+                             over a persistent root set that is split and
+                             reassigned after every iteration by the
+                             repetitions each root took, as PStaticLB does
+                             with node counts), all kept as ablations.
+                             Variants 2-5 take width 3 or 4, count_all = 1
+                             and no node budget (else BPIDA_EINVAL), solve
+                             the boards one at a time, synchronise the
+                             stream, use split_target as the number of
+                             search threads (variant 5: warps; 0 = every
+                             resident one) and report the load balance in
+                             bpida_stats; their solution is an optimal one
+                             (for 2, 3 and 5 the lexicographically first),
+                             and every count equals variant 0's */
     int reserved;
 } bpida_config;
 
@@ -159,13 +166,13 @@ typedef struct {
     double search_ms_device;/* sum of search kernel durations measured on
                                the device (first block start to last block
                                end, %globaltimer), any driver */
-    /* thread-parallel variants (2-4) only, zero otherwise: */
-    int tp_threads;         /* search threads */
+    /* variants 2-5 only, zero otherwise: */
+    int tp_threads;         /* search threads (variant 5: search warps) */
     int tp_pad;
     double lb_ratio;        /* load balance of the last board's next-to-last
                                iteration (its only one if it had one): the
-                               largest per-thread node count over the mean
-                               over all search threads */
+                               largest per-thread (variant 5: per-warp) node
+                               count over the mean over all of them */
     double lb_ratio_last;   /* the same for its final iteration */
     uint64_t tp_roots;      /* roots in the last board's final root set */
     uint64_t tp_balances;   /* variant 4: in-block balancing operations */

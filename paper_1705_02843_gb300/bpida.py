@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libbpida.so")
 
 OK, EINVAL, ENOMEM, ESTACK, EBUDGET, ETIMEOUT, ECUDA, ELIMIT, EINTERNAL = range(9)
 # bpida_config.variant values
-BLOCK_PARALLEL, PAPER_KERNEL, PSIMPLE, PSTATICLB, PFULLLB = range(5)
+BLOCK_PARALLEL, PAPER_KERNEL, PSIMPLE, PSTATICLB, PFULLLB, BPSTATIC = range(6)
 
 EXPORTS = (
     "bpida_max_len", "bpida_max_iters", "bpida_solve", "bpida_solve_ex", "bpida_set_timing",

@@ -685,7 +685,7 @@ bpida_status parse_settings(const bpida_config *cfg_in, int n, Settings &cfg)
         return BPIDA_EINVAL;
     if (cfg.driver != 0 && cfg.driver != 1)
         return BPIDA_EINVAL;
-    if (cfg.variant < 0 || cfg.variant > tp::PFULLLB)
+    if (cfg.variant < 0 || cfg.variant > tp::BPSTATIC)
         return BPIDA_EINVAL;
     if (cfg.variant >= tp::PSIMPLE && (cfg.width == 5 || cfg.count_all != 1 || cfg.budget != 0))
         return BPIDA_EINVAL;

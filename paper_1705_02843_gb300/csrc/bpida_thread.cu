@@ -18,6 +18,14 @@
 //              threads take the shallowest untried branches of busy threads
 //              of the same block through shared memory (DynamicLoadBalance).
 //
+// The same root-set machinery also runs the paper's BPIDA* with its own
+// static load balancing (Section 5, as an ablation): the search units are
+// warps (a block is one warp), each running Algorithm 1's BPDFS over its
+// roots (8 nodes per parallelPop, lane i applying action i mod 4, pushes at
+// ballot-reserved slots of a stack shared by the warp), and a root's load is
+// the number of repetitions of BPDFS's loop it took instead of its node
+// count. There is no dynamic load balancing.
+//
 // Root sets are built as the paper's CreateRootSet does, by an A*-style
 // expansion from the start (smallest f first), without duplicate detection:
 // a node is replaced in place by its children (every move but the inverse of
@@ -73,6 +81,9 @@ struct Ctrl {
     unsigned long long goal_key;  // (root index << 32) | thread of the recorded goal path
     unsigned long long balances;  // PFullLB balancing operations
     unsigned long long steals;    // PFullLB branches given to idle threads
+    unsigned long long reps;      // BPIDA*: repetitions of BPDFS's loop in this iteration
+    int err;                      // BPIDA*: a warp's overflow stack was full
+    int pad2;
     unsigned long long tot[4];    // totals of the last scans
 };
 
@@ -92,6 +103,7 @@ template <int W> struct Args {
     unsigned long long *bsum;         // scan block sums
     Root *scratch;                    // split regions
     uint8_t *path;                    // per thread: the first goal path it found
+    unsigned char *ovf;               // BPIDA*: per warp, an overflow stack in global memory
     uint8_t *out_moves;               // row of the current instance
     unsigned long long *out_nodes;    // row of the current instance
     int T;                            // search threads
@@ -744,6 +756,156 @@ __global__ void __launch_bounds__(TPB) k_search_tp(const Args<W> a, int L, int R
 }
 
 // ---------------------------------------------------------------------
+// The paper's BPIDA* search (Algorithm 1): one warp per unit
+// ---------------------------------------------------------------------
+constexpr int BPW_S = 512;        // shared-memory stack entries per warp
+constexpr int BPW_OVF = 2048;      // overflow stack entries per warp (global memory)
+
+constexpr size_t bpw_smem() { return SharedLut<4>::BYTES + (size_t)BPW_S * WarpStack<4>::ENTRY_BYTES; }
+
+// Warp u searches the roots [first_root(u), first_root(u + 1)) one after
+// another. For each root with f <= L, BPDFS: the stack starts with the root;
+// every repetition pops the top n <= 8 nodes (parallelPop), lanes 4q..4q+3
+// take node q, goal-test it (a goal is counted and not expanded), and lane
+// 4q + m applies move m; a child with f <= L is pushed at a ballot-reserved
+// slot (atomicPut), the others lower f_next. The repetitions a root took are
+// its load for the next iteration's rebalancing. When the shared stack
+// cannot take a repetition's children, its oldest half moves to the warp's
+// overflow stack in global memory, and comes back when the shared stack has
+// drained; a full overflow stack sets err (the call fails, nothing hangs).
+template <int W>
+__global__ void __launch_bounds__(32) k_search_bpw(const Args<W> a, int L, int R, unsigned long long E)
+{
+    typedef typename Geo<W>::B B;
+    constexpr int BITS = Geo<W>::BITS, S = BPW_S;
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char *lut = smem;
+    SharedLut<W>::load(lut, a.lut);
+    __syncthreads();
+    WarpStack<W> stk, ovf;
+    stk.init(smem + SharedLut<W>::BYTES, S);
+    ovf.init(a.ovf + (size_t)blockIdx.x * BPW_OVF * WarpStack<W>::ENTRY_BYTES, BPW_OVF);
+    const int lane = threadIdx.x & 31, q = lane >> 2, m = lane & 3;
+    const unsigned lt = (1u << lane) - 1u;
+    const B GOAL = goal_board<W>();
+    const int j0 = first_root(a.P, R, E, a.T, blockIdx.x), j1 = first_root(a.P, R, E, a.T, blockIdx.x + 1);
+    unsigned long long nodes = 0, goals = 0, reps_all = 0;
+    int fmin = INT_MAX;
+    unsigned goal_root = 0xffffffffu;
+    bool failed = false;
+    for (int j = j0; j < j1 && !failed; ++j) {
+        const Root r = a.A[j];
+        const int f = (int)r.g + (int)r.h;
+        if (f > L) {
+            fmin = min(fmin, f - L);
+            continue;
+        }
+        if (lane == 0)
+            stk.put(0, (B)r.b, sm_from_rec<W>(m_make(r.blank, r.last, (uint32_t)(L - f))), 0u);
+        __syncwarp();
+        int top = 1, ovn = 0;
+        unsigned long long reps = 0;
+        while (top > 0 || ovn > 0) {
+            if (top == 0) {
+                // refill from the overflow stack (its most recent entries)
+                const int k = min(ovn, S / 2);
+                for (int i = lane; i < k; i += 32) {
+                    B bb;
+                    uint32_t mm, oo;
+                    ovf.get(ovn - k + i, bb, mm, oo);
+                    stk.put(i, bb, mm, oo);
+                }
+                ovn -= k;
+                top = k;
+                __syncwarp();
+            }
+            const int n = min(8, top);
+            if (top + 3 * n > S) {
+                // room for 4n children: the oldest entries go to global memory
+                const int k = min(top - n, S / 2);
+                if (ovn + k > BPW_OVF) {
+                    failed = true;
+                    break;
+                }
+                for (int i = lane; i < k; i += 32) {
+                    B bb;
+                    uint32_t mm, oo;
+                    stk.get(i, bb, mm, oo);
+                    ovf.put(ovn + i, bb, mm, oo);
+                }
+                ovn += k;
+                __syncwarp();
+                for (int i0 = 0; i0 < top - k; i0 += 32) {
+                    const int i = i0 + lane;
+                    const bool ok = i < top - k;
+                    B bb = 0;
+                    uint32_t mm = 0, oo = 0;
+                    if (ok)
+                        stk.get(k + i, bb, mm, oo);
+                    __syncwarp();
+                    if (ok)
+                        stk.put(i, bb, mm, oo);
+                    __syncwarp();
+                }
+                top -= k;
+            }
+            // parallelPop: the top n nodes, four lanes per node
+            const bool act = q < n;
+            B b = 0;
+            uint32_t mt = 0, org = 0;
+            if (act)
+                stk.get(top - n + q, b, mt, org);
+            top -= n;
+            nodes += (unsigned long long)n;
+            ++reps;
+            __syncwarp();
+            const bool goal = act && b == GOAL;
+            const unsigned gm = __ballot_sync(FULL, goal && m == 0);
+            if (gm) {
+                goals += (unsigned long long)__popc(gm);
+                goal_root = min(goal_root, (unsigned)j);
+            }
+            const uint32_t sh_p = mt & 127u;
+            const int s = (int)((mt >> 11) & 255u);
+            // the (threadID mod #actions)th action
+            const bool legal = act && !goal && ((LegalMoves<W>::at_sh(sh_p) & ~((mt >> 7) & 15u)) >> m & 1u);
+            const uint32_t sh_np = sh_p + (uint32_t)(BITS * move_off<W>(m));
+            const unsigned t = BoardOps<W>::tile(b, sh_np);
+            const bool away = away_bit<W>(lut_row_sh<W>(lut, sh_p), m, t);
+            const bool push = legal && !(away && s < 2);
+            if (legal && away && s < 2)
+                fmin = min(fmin, 2 - s);
+            const B child = BoardOps<W>::flip(b, t * move_mul<W>(m), (m < 2) ? sh_np : sh_p);
+            const uint32_t cm = (sh_np + (mt & (255u << 11)) + ((1u << (3 - m)) << 7)) - (away ? (2u << 11) : 0u);
+            const unsigned pm = __ballot_sync(FULL, push);
+            if (push)
+                stk.put(top + __popc(pm & lt), child, cm, 0u);
+            top += __popc(pm);
+            __syncwarp();
+        }
+        if (lane == 0)
+            a.load[j] = reps;
+        reps_all += reps;
+    }
+    fmin = warp_min_int(fmin);
+    if (lane == 0) {
+        if (nodes)
+            atomicAdd(&a.ctrl->nodes, nodes);
+        atomicMax(&a.ctrl->maxload, nodes);
+        if (goals)
+            atomicAdd(&a.ctrl->goals, goals);
+        if (fmin != INT_MAX)
+            atomicMin(&a.ctrl->fmin_off, fmin);
+        if (reps_all)
+            atomicAdd(&a.ctrl->reps, reps_all);
+        if (goal_root != 0xffffffffu)
+            atomicMin(&a.ctrl->goal_key, (unsigned long long)goal_root << 32);
+        if (failed)
+            atomicOr(&a.ctrl->err, 1);
+    }
+}
+
+// ---------------------------------------------------------------------
 // Per-instance set-up and results
 // ---------------------------------------------------------------------
 template <int W> __global__ void k_init(const Args<W> a, const uint64_t *boards, int i)
@@ -801,6 +963,7 @@ template <int W> __global__ void k_reset_iter(const Args<W> a)
     c->goals = 0;
     c->goal_key = ~0ull;
     c->fmin_off = INT_MAX;
+    c->reps = 0;
 }
 
 template <int W> __global__ void k_close(const Args<W> a, int it, unsigned long long internal)
@@ -808,9 +971,10 @@ template <int W> __global__ void k_close(const Args<W> a, int it, unsigned long 
     a.out_nodes[it] = internal + a.ctrl->nodes;
 }
 
+// sols: the solution count, or ~0 for the goals the search counted
 template <int W>
 __global__ void k_finish(const Args<W> a, int i, int status, int length, int iters, int *out_len, int *out_iters,
-                         int *out_status, uint64_t *out_solutions)
+                         int *out_status, uint64_t *out_solutions, unsigned long long sols)
 {
     const bool ok = status == BPIDA_OK;
     if (ok) {
@@ -826,7 +990,7 @@ __global__ void k_finish(const Args<W> a, int i, int status, int length, int ite
         if (out_status)
             out_status[i] = status;
         if (out_solutions)
-            out_solutions[i] = ok ? a.ctrl->goals : 0ull;
+            out_solutions[i] = ok ? (sols != ~0ull ? sols : a.ctrl->goals) : 0ull;
     }
 }
 
@@ -839,7 +1003,7 @@ struct Buf {
 };
 
 struct Workspace {
-    Buf ctrl, A, B, load, est, P, want, soff, hpos, cntv, npos, heavy, bsum, scratch, path;
+    Buf ctrl, A, B, load, est, P, want, soff, hpos, cntv, npos, heavy, bsum, scratch, path, ovf;
     Ctrl *h_ctrl = nullptr;
     cudaError_t ensure(Buf &b, size_t bytes)
     {
@@ -858,7 +1022,7 @@ struct Workspace {
     void release()
     {
         Buf *all[] = {&ctrl, &A, &B, &load, &est, &P, &want, &soff, &hpos, &cntv, &npos, &heavy, &bsum, &scratch,
-                      &path};
+                      &path, &ovf};
         for (Buf *b : all) {
             if (b->p)
                 cudaFree(b->p);
@@ -887,7 +1051,7 @@ struct Totals {
     unsigned long long roots = 0, balances = 0, steals = 0;
 };
 
-template <int W, bool DLB>
+template <int W, bool DLB, bool BPW>
 bpida_status solve_one(const Settings &cfg, Workspace &ws, Args<W> a, const uint64_t *boards, int i, int grid,
                        int Rcap, size_t Scap, int *out_len, int *out_iters, int *out_status,
                        uint64_t *out_solutions, cudaStream_t st, Totals &tot, bpida_stats *stats)
@@ -902,8 +1066,9 @@ bpida_status solve_one(const Settings &cfg, Workspace &ws, Args<W> a, const uint
         cudaError_t e = cudaMemcpyAsync(ws.h_ctrl, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
         return e == cudaSuccess ? cudaStreamSynchronize(st) : e;
     };
-    auto finish = [&](int status, int length, int iters) -> bpida_status {
-        k_finish<W><<<1, 128, 0, st>>>(a, i, status, length, iters, out_len, out_iters, out_status, out_solutions);
+    auto finish = [&](int status, int length, int iters, unsigned long long sols = ~0ull) -> bpida_status {
+        k_finish<W><<<1, 128, 0, st>>>(a, i, status, length, iters, out_len, out_iters, out_status, out_solutions,
+                                      sols);
         TK(cudaGetLastError());
         return (bpida_status)status;
     };
@@ -978,7 +1143,10 @@ bpida_status solve_one(const Settings &cfg, Workspace &ws, Args<W> a, const uint
         TK(cudaMemsetAsync(a.load, 0, sizeof(unsigned long long) * (size_t)R, st));
         TK(fetch());
         const unsigned long long E = hc.tot[3];
-        k_search_tp<W, DLB><<<grid, TPB, search_smem<W, DLB>(), st>>>(a, L, R, E);
+        if (BPW)
+            k_search_bpw<W><<<grid, 32, bpw_smem(), st>>>(a, L, R, E);
+        else
+            k_search_tp<W, DLB><<<grid, TPB, search_smem<W, DLB>(), st>>>(a, L, R, E);
         TK(cudaGetLastError());
         k_close<W><<<1, 1, 0, st>>>(a, it, internal);
         TK(cudaGetLastError());
@@ -994,6 +1162,27 @@ bpida_status solve_one(const Settings &cfg, Workspace &ws, Args<W> a, const uint
         tot.ratio_last = ratio.back();
         tot.ratio_prev = ratio.size() >= 2 ? ratio[ratio.size() - 2] : ratio.back();
         stats->steps += 1;
+        if (BPW && hc.err)
+            return finish(BPIDA_ENOMEM, -1, it + 1);
+        if (hc.goals > 0 && BPW) {
+            // the path: the roots are in the order of their move sequences
+            // (CreateRootSet and the splits replace a node by its children in
+            // move order), so the first root with a goal, searched depth
+            // first in move order by one thread, gives the lexicographically
+            // first optimal solution (its counts are not used)
+            const unsigned long long sols = hc.goals;
+            const size_t gr = (size_t)(hc.goal_key >> 32);
+            Args<W> one = a;
+            one.A = a.B;
+            one.T = TPB;
+            TK(cudaMemcpyAsync(one.A, a.A + gr, sizeof(Root), cudaMemcpyDeviceToDevice, st));
+            TK(cudaMemsetAsync(a.P, 0, sizeof(unsigned long long), st));
+            k_reset_iter<W><<<1, 1, 0, st>>>(a);
+            k_search_tp<W, false><<<1, TPB, search_smem<W, false>(), st>>>(one, L, 1, 1ull);
+            TK(cudaGetLastError());
+            stats->launches += 2;
+            return finish(BPIDA_OK, L, it + 1, sols);
+        }
         if (hc.goals > 0)
             return finish(BPIDA_OK, L, it + 1);
         const int off = std::min(hc.fmin_off, hist_off);
@@ -1003,11 +1192,11 @@ bpida_status solve_one(const Settings &cfg, Workspace &ws, Args<W> a, const uint
             return finish(BPIDA_ELIMIT, -1, it + 1);
         L += off;
         ++it;
-        prev = hc.nodes;
+        prev = BPW ? hc.reps : hc.nodes;
     }
 }
 
-template <int W, bool DLB>
+template <int W, bool DLB, bool BPW>
 bpida_status solve_wd(const Settings &cfg, const uint64_t *boards, int n, int *out_len, uint8_t *out_moves,
                       uint64_t *out_nodes, int *out_iters, int *out_status, uint64_t *out_solutions, cudaStream_t st,
                       bpida_stats *stats)
@@ -1021,14 +1210,20 @@ bpida_status solve_wd(const Settings &cfg, const uint64_t *boards, int n, int *o
         g_ws[dev] = new Workspace();
     Workspace &ws = *g_ws[dev];
 
-    constexpr size_t smem = search_smem<W, DLB>();
-    static int bpsm = 0;  // per (W, DLB) instantiation
-    if (bpsm == 0)
-        TK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_search_tp<W, DLB>, TPB, smem));
+    // search units: threads, or warps (BPIDA*: a block is one warp)
+    const int unit_threads = BPW ? 32 : TPB;
+    const size_t smem = BPW ? bpw_smem() : search_smem<W, DLB>();
+    static int bpsm = 0;  // per (W, DLB, BPW) instantiation
+    if (bpsm == 0) {
+        if (BPW)
+            TK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_search_bpw<W>, 32, smem));
+        else
+            TK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_search_tp<W, DLB>, TPB, smem));
+    }
     if (bpsm < 1)
         return BPIDA_EINVAL;
-    const int grid = cfg.threads > 0 ? (cfg.threads + TPB - 1) / TPB : sms * bpsm;
-    const int T = grid * TPB;
+    const int grid = cfg.threads > 0 ? (BPW ? cfg.threads : (cfg.threads + TPB - 1) / TPB) : sms * bpsm;
+    const int T = BPW ? grid : grid * TPB;
     const long long rcap = (long long)(cfg.variant == PSIMPLE ? 2 : 32) * T + 4096;
     if (rcap > (1ll << 30))
         return BPIDA_ENOMEM;
@@ -1050,7 +1245,9 @@ bpida_status solve_wd(const Settings &cfg, const uint64_t *boards, int n, int *o
     TK(ws.ensure(ws.heavy, sizeof(unsigned) * (size_t)Rcap));
     TK(ws.ensure(ws.bsum, u64 * ((size_t)Rcap / SC_B + 2)));
     TK(ws.ensure(ws.scratch, sizeof(Root) * Scap));
-    TK(ws.ensure(ws.path, (size_t)T * Geo<W>::MAXLEN));
+    TK(ws.ensure(ws.path, (size_t)std::max(T, TPB) * Geo<W>::MAXLEN));
+    if (BPW)
+        TK(ws.ensure(ws.ovf, (size_t)T * BPW_OVF * WarpStack<W>::ENTRY_BYTES));
     if (!ws.h_ctrl)
         TK(cudaMallocHost((void **)&ws.h_ctrl, sizeof(Ctrl)));
 
@@ -1071,20 +1268,21 @@ bpida_status solve_wd(const Settings &cfg, const uint64_t *boards, int n, int *o
     a.bsum = (unsigned long long *)ws.bsum.p;
     a.scratch = (Root *)ws.scratch.p;
     a.path = (uint8_t *)ws.path.p;
+    a.ovf = (unsigned char *)ws.ovf.p;
     a.out_moves = out_moves;
     a.out_nodes = (unsigned long long *)out_nodes;
     a.T = T;
     a.lut = make_move_lut<W>();
 
     stats->grid_blocks = grid;
-    stats->block_threads = TPB;
+    stats->block_threads = unit_threads;
     stats->sm_count = sms;
     stats->tp_threads = T;
     bpida_status first = BPIDA_OK;
     Totals tot;
     unsigned long long balances = 0, steals = 0;
     for (int i = 0; i < n; ++i) {
-        const bpida_status s = solve_one<W, DLB>(cfg, ws, a, boards, i, grid, Rcap, Scap, out_len, out_iters,
+        const bpida_status s = solve_one<W, DLB, BPW>(cfg, ws, a, boards, i, grid, Rcap, Scap, out_len, out_iters,
                                                  out_status, out_solutions, st, tot, stats);
         // per-instance outcomes (invalid board, length cap) go to out_status
         if (s == BPIDA_ECUDA || s == BPIDA_ENOMEM)
@@ -1107,16 +1305,16 @@ bpida_status solve(const Settings &cfg, const uint64_t *boards, int n, int *out_
                    uint64_t *out_nodes, int *out_iters, int *out_status, uint64_t *out_solutions, cudaStream_t st,
                    bpida_stats *stats)
 {
+#define TP_SOLVE(W_, DLB_, BPW_)                                                                              \
+    solve_wd<W_, DLB_, BPW_>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status, out_solutions, \
+                             st, stats)
+    if (cfg.variant == BPSTATIC)
+        return cfg.width == 3 ? TP_SOLVE(3, false, true) : TP_SOLVE(4, false, true);
     const bool dlb = cfg.variant == PFULLLB;
     if (cfg.width == 3)
-        return dlb ? solve_wd<3, true>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status,
-                                       out_solutions, st, stats)
-                   : solve_wd<3, false>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status,
-                                        out_solutions, st, stats);
-    return dlb ? solve_wd<4, true>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status,
-                                   out_solutions, st, stats)
-               : solve_wd<4, false>(cfg, boards, n, out_len, out_moves, out_nodes, out_iters, out_status,
-                                    out_solutions, st, stats);
+        return dlb ? TP_SOLVE(3, true, false) : TP_SOLVE(3, false, false);
+    return dlb ? TP_SOLVE(4, true, false) : TP_SOLVE(4, false, false);
+#undef TP_SOLVE
 }
 
 void release(int dev)

@@ -1,5 +1,6 @@
-// Internal interface of the thread-parallel IDA* ablations (bpida_thread.cu),
-// reached through bpida_solve_ex with variant = 2, 3 or 4.
+// Internal interface of the thread-parallel IDA* ablations and of the paper's
+// BPIDA* with its static load balancing (bpida_thread.cu), reached through
+// bpida_solve_ex with variant = 2, 3, 4 or 5.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -9,12 +10,12 @@
 namespace bp {
 namespace tp {
 
-enum { PSIMPLE = 2, PSTATICLB = 3, PFULLLB = 4 };
+enum { PSIMPLE = 2, PSTATICLB = 3, PFULLLB = 4, BPSTATIC = 5 };
 
 struct Settings {
     int width;    // 3 or 4
-    int variant;  // PSIMPLE, PSTATICLB or PFULLLB
-    int threads;  // search threads; 0 = every resident thread of the search kernel
+    int variant;  // PSIMPLE, PSTATICLB, PFULLLB or BPSTATIC
+    int threads;  // search threads (BPSTATIC: warps); 0 = all resident ones of the search kernel
 };
 
 // Solves the n boards one after another (one instance per run, as in the

@@ -48,17 +48,18 @@ def test_config_struct_layout():
 
 
 def test_variant_arguments_are_checked_before_any_work(lib):
-    """Unknown variants, and thread-parallel variants (2-4) with a 24-puzzle
+    """Unknown variants, and the ablation variants 2-5 with a 24-puzzle
     width, first-solution mode or a node budget, are rejected on the host."""
     b = bpida.load()
-    bad = [dict(variant=5), dict(variant=-1), dict(variant=bpida.PSIMPLE, width=5),
-           dict(variant=bpida.PSTATICLB, count_all=False), dict(variant=bpida.PFULLLB, node_budget=10)]
+    bad = [dict(variant=6), dict(variant=-1), dict(variant=bpida.PSIMPLE, width=5),
+           dict(variant=bpida.PSTATICLB, count_all=False), dict(variant=bpida.PFULLLB, node_budget=10),
+           dict(variant=bpida.BPSTATIC, width=5), dict(variant=bpida.BPSTATIC, count_all=False)]
     for kw in bad:
         width = kw.pop("width", 4)
         cfg = bpida.make_config(width, **kw)
         rc = b.bpida_solve_ex(ctypes.byref(cfg), None, 0, None, None, None, None, None, None, None)
         assert rc == bpida.EINVAL, kw
-    for v in (bpida.PSIMPLE, bpida.PSTATICLB, bpida.PFULLLB):
+    for v in (bpida.PSIMPLE, bpida.PSTATICLB, bpida.PFULLLB, bpida.BPSTATIC):
         cfg = bpida.make_config(4, variant=v)
         assert b.bpida_solve_ex(ctypes.byref(cfg), None, 0, None, None, None, None, None, None, None) == bpida.OK
 

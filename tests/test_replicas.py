@@ -64,6 +64,8 @@ def test_bench_pattern_database_constants_cover_every_partition():
     for table in (bench.INSTR_PER_EXPANSION_PDB, bench.TRAFFIC_PER_LAUNCH_PDB, bench.ALU_PIPE_SHARE_PDB):
         assert set(table) == parts
         assert all(v is not None and v > 0 for v in table.values())
-    assert 0.5 < bench.ALU_PIPE_SHARE < 1.0
+    for form in ("batched", "plain"):
+        k = bench.KERNEL_COUNTERS[form]
+        assert 0.0 < k["alu_pipe_share"] < 1.0 and k["instr_per_expansion"] > 1.0
     out = subprocess.run([sys.executable, bench.__file__, "--help"], capture_output=True, text=True, check=True).stdout
     assert "--pdb {%s}" % ",".join(sorted(parts)) in out

@@ -1,5 +1,7 @@
 """Thread-parallel IDA* ablations (variants 2-4: PSimple, PStaticLB, PFullLB)
-against the CPU oracle and against an independent model of their load
+and the paper's BPIDA* with its static load balancing (variant 5: one warp
+per search unit, roots rebalanced by the repetitions they took) against the
+CPU oracle, and PSimple/PStaticLB against an independent model of their load
 balance.
 
 Every integer result must equal the oracle's: status, optimal length, nodes
@@ -28,7 +30,7 @@ from tests import puzzle_ref as P
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-VARIANTS = [bpida.PSIMPLE, bpida.PSTATICLB, bpida.PFULLLB]
+VARIANTS = [bpida.PSIMPLE, bpida.PSTATICLB, bpida.PFULLLB, bpida.BPSTATIC]
 
 
 def tp_solve(W, boards_tiles, variant, threads=0):
@@ -63,7 +65,10 @@ def test_walks15_match_oracle(variant, threads):
     rc, got, st = tp_solve(4, tiles, variant, threads)
     assert rc == bpida.OK
     check(4, tiles, got, oracle.solve_batch(4, np.array(tiles, dtype=np.uint8)), variant)
-    assert st["tp_threads"] == (threads + 127) // 128 * 128 if threads else st["tp_threads"] > 0
+    if variant == bpida.BPSTATIC:  # search units are warps
+        assert st["tp_threads"] == threads if threads else st["tp_threads"] > 0
+    else:
+        assert st["tp_threads"] == (threads + 127) // 128 * 128 if threads else st["tp_threads"] > 0
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
