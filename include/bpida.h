@@ -95,7 +95,7 @@ typedef struct {
     int split_target;     /* max frontier records per instance; 0 = auto */
     int warps_per_block;  /* search kernel block size in warps; 0 = auto */
     int stack_entries;    /* per-warp shared-memory stack, 0 = auto
-                             (480 for width 4, else 512); one of 256,
+                             (width 4: 480, 5: 384, 3: 512); one of 256,
                              384, 480, 512, 768, 1024 */
     int exit_fraction_pct;/* percentage of warps that must have run out of
                              work before busy warps hand their stacks back
@@ -140,7 +140,14 @@ typedef struct {
                              resident one) and report the load balance in
                              bpida_stats; their solution is an optimal one
                              (for 2, 3 and 5 the lexicographically first),
-                             and every count equals variant 0's */
+                             and every count equals variant 0's; 6 = block
+                             per subtree group: variant 0's queue and
+                             hand-back, but the warps of a block share one
+                             stack (warps_per_block x stack_entries
+                             entries), a round pops one node per thread,
+                             and children are placed by a block-wide prefix
+                             (the autotuner's other mode; width 3 or 4, one
+                             iteration per step) */
     int reserved;
 } bpida_config;
 

@@ -1,16 +1,20 @@
 """Autotuner for the solver's launch knobs.
 
-Tunes the frontier cap (root-split size), warps per block, per-warp stack
-size, hand-back threshold and minimum rounds before hand-back by coordinate
-descent on measured throughput (instances/s) of a sample workload, in either
-form: "plain" (one solve call per board) or "batched" (one call for all).
-A candidate is accepted only if every result (length, nodes per iteration,
-first solution, status) equals the expected results given by the caller
-(normally the stored oracle results of the sample), so tuning can never
-trade exactness for speed. The best configuration is cached per (GPU name,
-SM count, width, form) in a JSON file.
+Tunes the search mode (a warp or a block per subtree group: bpida_config
+variant 0 or 6), the frontier cap (root-split size), warps per block,
+per-warp stack size, hand-back threshold and minimum rounds before
+hand-back by coordinate descent on measured throughput (instances/s) of a
+sample workload, in either form: "plain" (one solve call per board) or
+"batched" (one call for all). A candidate is accepted only if every result
+(length, nodes per iteration, first solution, status) equals the expected
+results given by the caller (normally the stored oracle results of the
+sample), so tuning can never trade exactness for speed. The best
+configuration is cached per (GPU name, SM count, width, form) in a JSON file
+(BPIDA_TUNE_CACHE, else ~/.cache/bpida/tune.json), which bpida.solve reads
+to fill the configuration fields a caller leaves at 0.
 
     python -m paper_1705_02843_gb300.autotune --workload perms15_100 --form plain
+    python -m paper_1705_02843_gb300.autotune --workload walks24_1024 --form batched --budget 50000000
 """
 from __future__ import annotations
 
@@ -27,38 +31,54 @@ from . import bpida
 from . import inputs as I
 
 KNOBS = {
+    "variant": [0, 6],
     "split_target": [1024, 2048, 4096, 8192],
     "warps_per_block": [2, 4, 8],
-    "stack_entries": [384, 512, 768],
+    "stack_entries": [384, 480, 512, 768],
     "exit_fraction_pct": [5, 10, 25],
     "min_rounds": [32, 64, 128],
 }
-DEFAULT = {"split_target": 4096, "warps_per_block": 4, "stack_entries": 512,
+# The library's defaults (bpida.cu) for each width.
+DEFAULT = {"variant": 0, "split_target": 4096, "warps_per_block": 4, "stack_entries": 480,
            "exit_fraction_pct": 10, "min_rounds": 64}
 
 
+def defaults(width: int) -> Dict[str, int]:
+    d = dict(DEFAULT)
+    if width != 4:
+        d["stack_entries"] = 384 if width == 5 else 512
+    return d
+
+
+def knob_values(width: int) -> Dict[str, List[int]]:
+    """The values tried for each knob (block mode is for widths 3 and 4)."""
+    k = {name: list(v) for name, v in KNOBS.items()}
+    if width == 5:
+        k["variant"] = [0]
+        k["stack_entries"] = [256, 384, 512, 768, 1024]
+    return k
+
+
 def cache_path() -> str:
-    return os.environ.get("BPIDA_TUNE_CACHE",
-                          os.path.join(os.path.expanduser("~"), ".cache", "bpida", "tune.json"))
+    return bpida.tune_cache_path()
 
 
 def device_key(width: int, form: str) -> str:
-    p = torch.cuda.get_device_properties(torch.cuda.current_device())
-    return "%s|%d|w%d|%s" % (p.name, p.multi_processor_count, width, form)
+    return bpida.tune_key(width, form)
 
 
-def _config(width: int, knobs: Dict[str, int]) -> bpida.Config:
-    return bpida.make_config(width, **knobs)
+def _config(width: int, knobs: Dict[str, int], node_budget: int = 0) -> bpida.Config:
+    return bpida.make_config(width, node_budget=node_budget, **knobs)
 
 
-def _run(boards: torch.Tensor, width: int, form: str, knobs: Dict[str, int]):
-    cfg = _config(width, knobs)
+def _run(boards: torch.Tensor, width: int, form: str, knobs: Dict[str, int], node_budget: int = 0):
+    cfg = _config(width, knobs, node_budget)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     if form == "batched":
-        sols = [bpida.solve(boards, width, cfg)]
+        sols = [bpida.solve(boards, width, cfg, tuned=False)]
     else:
-        sols = [bpida.solve(boards[i:i + 1], width, cfg) for i in range(boards.shape[0])]
+        sols = [bpida.solve(boards[i:i + 1], width, cfg, tuned=False) for i in range(boards.shape[0])]
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     if any(s.status != bpida.OK for s in sols):
@@ -75,30 +95,33 @@ def _same(res: Sequence[dict], expected: Sequence[dict]) -> bool:
 
 
 def tune(boards: torch.Tensor, width: int, form: str, expected: Sequence[dict],
-         repeats: int = 2, rounds: int = 2, log=print) -> Dict[str, int]:
-    """Coordinate descent from DEFAULT; returns the best knob setting whose
-    results equal `expected` (per-board dicts with status/length/nodes/moves)."""
+         repeats: int = 2, rounds: int = 2, log=print, node_budget: int = 0) -> Dict[str, int]:
+    """Coordinate descent from the library's defaults; returns the best knob
+    setting whose results equal `expected` (per-board dicts with
+    status/length/nodes/moves)."""
     n = boards.shape[0]
+    start = defaults(width)
+    values = knob_values(width)
 
     def score(knobs):
         best = None
         for _ in range(repeats):
-            res, dt = _run(boards, width, form, knobs)
+            res, dt = _run(boards, width, form, knobs, node_budget)
             if res is None or not _same(res, expected):
                 return None
             best = dt if best is None else min(best, dt)
         return n / best
 
-    _run(boards, width, form, DEFAULT)  # warm-up (graphs, workspace)
-    cur = dict(DEFAULT)
+    _run(boards, width, form, start, node_budget)  # warm-up (graphs, workspace)
+    cur = dict(start)
     cur_s = score(cur)
     if cur_s is None:
         raise RuntimeError("the default configuration does not reproduce the expected results")
     log("default %s: %.1f inst/s" % (cur, cur_s))
     for _ in range(rounds):
         improved = False
-        for knob, values in KNOBS.items():
-            for v in values:
+        for knob, vals in values.items():
+            for v in vals:
                 if v == cur[knob]:
                     continue
                 cand = dict(cur, **{knob: v})
@@ -126,16 +149,13 @@ def save(width: int, form: str, knobs: Dict[str, int], path: Optional[str] = Non
 
 def load_config(width: int, form: str, path: Optional[str] = None) -> Optional[bpida.Config]:
     """The cached configuration for this GPU, width and form, or None."""
-    path = path or cache_path()
-    if not os.path.exists(path):
-        return None
-    with open(path) as f:
-        doc = json.load(f)
-    knobs = doc.get(device_key(width, form))
+    knobs = bpida.tuned_knobs(width, form, path)
     return _config(width, knobs) if knobs else None
 
 
 def _golden_expected(workload: str, indices: List[int]) -> Optional[List[dict]]:
+    """Stored oracle results; a board the oracle stopped at its node budget
+    reports only its completed iterations."""
     here = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     path = os.path.join(here, "tests", "golden", workload + ".json")
     if not os.path.exists(path):
@@ -145,8 +165,10 @@ def _golden_expected(workload: str, indices: List[int]) -> Optional[List[dict]]:
     out = []
     for i in indices:
         r = by_index[i]
-        out.append({"status": r["status"], "length": r["length"], "nodes": r["nodes"],
-                    "moves": [int(c) for c in r["moves"]]})
+        ok = r["status"] == 0
+        out.append({"status": r["status"], "length": r["length"] if ok else -1,
+                    "nodes": r["nodes"] if ok else r["nodes"][:-1],
+                    "moves": [int(c) for c in r["moves"]] if ok else []})
     return out
 
 
@@ -155,6 +177,8 @@ def main():
     ap.add_argument("--workload", default="perms15_100", choices=sorted(I.WORKLOADS))
     ap.add_argument("--form", default="plain", choices=["plain", "batched"])
     ap.add_argument("--sample", type=int, default=40, help="boards of the workload to tune on")
+    ap.add_argument("--budget", type=int, default=0, help="node budget per board (as the stored results' oracle)")
+    ap.add_argument("--rounds", type=int, default=2)
     ap.add_argument("--no-save", action="store_true")
     args = ap.parse_args()
     insts = I.WORKLOADS[args.workload]()
@@ -163,13 +187,15 @@ def main():
     sample = [insts[i] for i in idx]
     arr = I.packed_array(sample)
     boards = torch.from_numpy(arr.view(np.int64)).cuda()
+    if W == 5:
+        boards = boards.reshape(-1, 2)
     expected = _golden_expected(args.workload, idx)
     if expected is None:
         # no stored oracle results: the default configuration's results,
         # which the parity tests check against the oracle, are the reference
-        res, _ = _run(boards, W, args.form, DEFAULT)
+        res, _ = _run(boards, W, args.form, defaults(W), args.budget)
         expected = res
-    best = tune(boards, W, args.form, expected)
+    best = tune(boards, W, args.form, expected, rounds=args.rounds, node_budget=args.budget)
     if not args.no_save:
         save(W, args.form, best)
         print("saved to", cache_path())

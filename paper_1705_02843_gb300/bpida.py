@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libbpida.so")
 
 OK, EINVAL, ENOMEM, ESTACK, EBUDGET, ETIMEOUT, ECUDA, ELIMIT, EINTERNAL = range(9)
 # bpida_config.variant values
-BLOCK_PARALLEL, PAPER_KERNEL, PSIMPLE, PSTATICLB, PFULLLB, BPSTATIC = range(6)
+BLOCK_PARALLEL, PAPER_KERNEL, PSIMPLE, PSTATICLB, PFULLLB, BPSTATIC, BLOCK_MODE = range(7)
 
 EXPORTS = (
     "bpida_max_len", "bpida_max_iters", "bpida_solve", "bpida_solve_ex", "bpida_set_timing",
@@ -253,6 +253,54 @@ class Solution:
         return out
 
 
+# Configuration fields the autotuner caches (bpida_config names; the search
+# mode is `variant`, 0 = a warp and 6 = a block per subtree group).
+TUNE_FIELDS = ("variant", "split_target", "warps_per_block", "stack_entries", "exit_fraction_pct", "min_rounds")
+_tune = {"path": None, "mtime": None, "doc": {}}
+
+
+def tune_cache_path() -> str:
+    """The autotuner's cache file: BPIDA_TUNE_CACHE, else ~/.cache/bpida/tune.json."""
+    return os.environ.get("BPIDA_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "bpida", "tune.json"))
+
+
+def tune_key(width: int, form: str, device=None) -> str:
+    """Cache key: GPU name, SM count, board width, form ("plain": calls of at
+    most 8 boards, "batched": larger calls)."""
+    p = torch.cuda.get_device_properties(device if device is not None else torch.cuda.current_device())
+    return "%s|%d|w%d|%s" % (p.name, p.multi_processor_count, width, form)
+
+
+def tuned_knobs(width: int, form: str, path: Optional[str] = None, device=None) -> dict:
+    """The cached knobs for this GPU, width and form ({} without an entry)."""
+    import json
+
+    path = path or tune_cache_path()
+    if not path or not os.path.exists(path):
+        return {}
+    mtime = os.path.getmtime(path)
+    if _tune["path"] != path or _tune["mtime"] != mtime:
+        with open(path) as f:
+            _tune.update(path=path, mtime=mtime, doc=json.load(f))
+    return {k: int(v) for k, v in _tune["doc"].get(tune_key(width, form, device), {}).items() if k in TUNE_FIELDS}
+
+
+def resolve_config(cfg: "Config", width: int, n: int, device=None) -> "Config":
+    """A copy of cfg whose fields left at 0 take the autotuner's cached values
+    for this GPU, width and call size (variant 0 takes the tuned search
+    mode); cfg itself without a cache entry."""
+    knobs = tuned_knobs(width, "plain" if n <= 8 else "batched", device=device)
+    if not knobs:
+        return cfg
+    out = Config()
+    ctypes.memmove(ctypes.byref(out), ctypes.byref(cfg), ctypes.sizeof(Config))
+    for k, v in knobs.items():
+        if getattr(out, k) == 0:
+            setattr(out, k, v)
+    return out
+
+
 def make_config(width: int = 4, split_target: int = 0, warps_per_block: int = 0,
                 stack_entries: int = 0, exit_fraction_pct: int = 0, min_rounds: int = 0,
                 node_budget: int = 0, driver: int = 0, min_pass_us: int = 0,
@@ -262,7 +310,8 @@ def make_config(width: int = 4, split_target: int = 0, warps_per_block: int = 0,
 
 
 def solve(boards: torch.Tensor, width: int = 4, config: Optional[Config] = None,
-          stream: Optional[torch.cuda.Stream] = None, pdb: Optional["PatternDb"] = None) -> Solution:
+          stream: Optional[torch.cuda.Stream] = None, pdb: Optional["PatternDb"] = None,
+          tuned: bool = True) -> Solution:
     """Solve packed boards already on the GPU.
 
     ``boards``: CUDA int64 tensor, shape (n,) for width 3/4, (n, 2) for 5,
@@ -271,7 +320,9 @@ def solve(boards: torch.Tensor, width: int = 4, config: Optional[Config] = None,
     ``stream`` (default: the current stream) and returns without waiting
     (graph driver): the outputs are valid once that stream has reached the
     end of the call. With ``pdb`` the heuristic is that pattern database
-    (bpida_solve_pdb), else the Manhattan distance.
+    (bpida_solve_pdb), else the Manhattan distance. With ``tuned`` (and the
+    Manhattan distance) the configuration fields left at 0 take the
+    autotuner's cached values for this GPU (resolve_config).
     """
     lib = load()
     if not boards.is_cuda:
@@ -285,6 +336,8 @@ def solve(boards: torch.Tensor, width: int = 4, config: Optional[Config] = None,
     cfg = config if config is not None else make_config(width)
     cfg.width = width
     dev = boards.device
+    if tuned and pdb is None:
+        cfg = resolve_config(cfg, width, n, dev)
     ml, mi = lib.bpida_max_len(width), lib.bpida_max_iters(width)
     out_len = torch.empty(n, dtype=torch.int32, device=dev)
     out_moves = torch.empty((n, ml), dtype=torch.uint8, device=dev)

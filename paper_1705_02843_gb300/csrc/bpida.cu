@@ -288,12 +288,19 @@ struct Geometry {
     bool fuse;
 };
 
+// variant 0: warp per subtree group; 1: the paper's kernel; 6: block per
+// subtree group (the autotuner's other mode, widths 3 and 4)
+constexpr int VARIANT_BLOCK = 6;
 template <int W, int S, bool PDB> void (*search_kernel(int variant, bool fuse))(const Dev<W>)
 {
-    if constexpr (PDB)
+    if constexpr (PDB) {
         return fuse ? k_search<W, S, true, true> : k_search<W, S, false, true>;
-    else
+    } else {
+        if constexpr (W <= 4)
+            if (variant == VARIANT_BLOCK)
+                return k_search_block<W, S>;
         return variant == 1 ? k_search_paper<W, S> : fuse ? k_search<W, S, true> : k_search<W, S, false>;
+    }
 }
 
 // The whole solve as one graph (k_set_desc is launched before it):
@@ -666,9 +673,11 @@ bpida_status parse_settings(const bpida_config *cfg_in, int n, Settings &cfg)
     cfg.count_all = cfg_in ? cfg_in->count_all : 1;
     cfg.split_target = cfg_in ? cfg_in->split_target : 0;
     cfg.wpb = (cfg_in && cfg_in->warps_per_block > 0) ? cfg_in->warps_per_block : 4;
-    // 15-puzzle: 480 entries keep seven 4-warp search blocks per SM (more
-    // resident warps outweigh the extra stack spills); otherwise 512
-    cfg.S = (cfg_in && cfg_in->stack_entries > 0) ? cfg_in->stack_entries : (cfg.width == 4 ? 480 : 512);
+    // more resident warps outweigh the extra stack spills: 15-puzzle 480
+    // entries (seven 4-warp search blocks per SM), 24-puzzle 384 (24-byte
+    // entries); 8-puzzle 512
+    cfg.S = (cfg_in && cfg_in->stack_entries > 0) ? cfg_in->stack_entries
+                                                  : (cfg.width == 4 ? 480 : cfg.width == 5 ? 384 : 512);
     cfg.exit_pct = (cfg_in && cfg_in->exit_fraction_pct > 0) ? cfg_in->exit_fraction_pct : 10;
     cfg.min_rounds = (cfg_in && cfg_in->min_rounds > 0) ? cfg_in->min_rounds : 64;
     cfg.driver = cfg_in ? cfg_in->driver : 0;
@@ -685,9 +694,12 @@ bpida_status parse_settings(const bpida_config *cfg_in, int n, Settings &cfg)
         return BPIDA_EINVAL;
     if (cfg.driver != 0 && cfg.driver != 1)
         return BPIDA_EINVAL;
-    if (cfg.variant < 0 || cfg.variant > tp::BPSTATIC)
+    if (cfg.variant < 0 || cfg.variant > VARIANT_BLOCK)
         return BPIDA_EINVAL;
-    if (cfg.variant >= tp::PSIMPLE && (cfg.width == 5 || cfg.count_all != 1 || cfg.budget != 0))
+    if (cfg.variant >= tp::PSIMPLE && cfg.variant <= tp::BPSTATIC &&
+        (cfg.width == 5 || cfg.count_all != 1 || cfg.budget != 0))
+        return BPIDA_EINVAL;
+    if (cfg.variant == VARIANT_BLOCK && cfg.width == 5)
         return BPIDA_EINVAL;
     if (cfg.count_all != 0 && cfg.count_all != 1)
         return BPIDA_EINVAL;
@@ -729,7 +741,7 @@ bpida_status bpida_solve_ex(const bpida_config *cfg_in, const uint64_t *boards, 
         return BPIDA_EINVAL;
     std::lock_guard<std::mutex> lock(g_mu);
     cudaStream_t st = (cudaStream_t)stream;
-    if (cfg.variant >= tp::PSIMPLE) {
+    if (cfg.variant >= tp::PSIMPLE && cfg.variant <= tp::BPSTATIC) {
         tp::Settings ts;
         ts.width = cfg.width;
         ts.variant = cfg.variant;

@@ -1316,6 +1316,329 @@ __global__ void k_search(const Dev<W> a)
 }
 
 // ---------------------------------------------------------------------
+// Block-per-subtree search (bpida_config.variant = 6), the other mode of the
+// autotuner: all warps of a block share one stack of S entries per warp, as
+// in Algorithm 1 with a block larger than a warp. Each round pops up to
+// blockDim nodes (one per thread); a thread's children go to slots from a
+// block-wide prefix of the per-thread counts (bit-sliced ballots within a
+// warp, warp totals through shared memory), with block barriers between the
+// pop and the pushes. Everything else is as in k_search: runs of records of
+// one instance from the pass's queue, node budget and first-solution checks
+// every 32 rounds, hand-back once enough warps have run dry. 8- and
+// 15-puzzle, Manhattan distance.
+// ---------------------------------------------------------------------
+template <int W, int S>
+__global__ void k_search_block(const Dev<W> a)
+{
+    typedef typename Geo<W>::B B;
+    static_assert(W <= 4, "block mode: 8- and 15-puzzle");
+    constexpr int BITS = Geo<W>::BITS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_cnt[32];
+    __shared__ int s_h, s_first, s_flag, s_fmin;
+    __shared__ unsigned s_inst;
+    unsigned char *lut = smem;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nthr = blockDim.x, nw = nthr >> 5;
+    const int SB = S * nw;  // the block's stack entries
+    if (tid == 0)
+        atomicMin(&a.ctrl->t_start, global_ns());
+    SharedLut<W>::load(lut, a.lut);
+    if (tid == 0)
+        s_fmin = INT_MAX;
+    __syncthreads();
+    WarpStack<W> stk;
+    stk.init(smem + SearchSmem<W>::TABLES, SB);
+    const Rec<W> *in = a.ctrl->qi ? a.q1 : a.q0;
+    Rec<W> *out = a.ctrl->qi ? a.q0 : a.q1;
+    const bool frontier = a.ctrl->first_pass != 0;
+    const int n_act = a.ctrl->n_active;
+    const int n_front = a.ctrl->n_front;
+    const unsigned *act_list = a.ctrl->cur ? a.act1 : a.act0;
+    const bool first_only = a.desc->first_only != 0;
+    const unsigned lt = (1u << lane) - 1u;
+    const B GOAL = goal_board<W>();
+    const int n_in = a.ctrl->n_in;
+    const int chunk = max(1, min(nthr, n_in / (int)(gridDim.x * 4)));
+    int rounds = 0;
+    bool stop = false;
+    unsigned acc_inst = 0xffffffffu;
+    unsigned long long acc_nodes = 0, tot_nodes = 0;  // the same in every thread
+    int fmin = INT_MAX;
+    // block-wide: publishes the counters of acc_inst (every thread calls it)
+    auto publish = [&]() {
+        const int fm = warp_min_int(fmin);
+        if (lane == 0 && fm != INT_MAX)
+            atomicMin(&s_fmin, fm);
+        __syncthreads();
+        if (tid == 0 && acc_inst != 0xffffffffu) {
+            if (acc_nodes)
+                atomicAdd(&a.cnt.search_nodes[acc_inst], acc_nodes);
+            if (s_fmin != INT_MAX)
+                atomicMin(&a.cnt.fnext_off[acc_inst], s_fmin);
+        }
+        __syncthreads();
+        if (tid == 0)
+            s_fmin = INT_MAX;
+        acc_nodes = 0;
+        fmin = INT_MAX;
+    };
+    // block-wide: stack entries [from, from + k) to the next pass
+    auto hand_back = [&](int from, int k, unsigned inst) {
+        if (k <= 0)
+            return;
+        if (tid == 0)
+            s_h = atomicAdd(&a.ctrl->out_count, k);
+        __syncthreads();
+        const int base = s_h;
+        __syncthreads();
+        if (base + k > a.Q) {
+            if (tid == 0)
+                atomicOr(&a.ctrl->err, ERR_QUEUE);
+            return;
+        }
+        for (int j = tid; j < k; j += nthr) {
+            B b;
+            uint32_t m, o;
+            stk.get(from + j, b, m, o);
+            Rec<W> r;
+            r.b = b;
+            r.meta = rec_from_sm<W>(m);
+            r.inst = inst;
+            r.origin = o;
+            r.pm = 0;
+            out[base + j] = r;
+        }
+    };
+    auto hand_back_input = [&](int from, int to) {
+        const int k = to - from;
+        if (k <= 0)
+            return;
+        if (tid == 0)
+            s_h = atomicAdd(&a.ctrl->out_count, k);
+        __syncthreads();
+        const int base = s_h;
+        __syncthreads();
+        if (base + k > a.Q) {
+            if (tid == 0)
+                atomicOr(&a.ctrl->err, ERR_QUEUE);
+            return;
+        }
+        for (int j = tid; j < k; j += nthr)
+            out[base + j] = load_rec<W>(a, frontier, n_act, n_front, act_list, in, from + j);
+    };
+
+    for (;;) {
+        if (tid == 0)
+            s_h = atomicAdd(&a.ctrl->head, chunk);
+        __syncthreads();
+        const int h = s_h;
+        __syncthreads();
+        if (h >= n_in)
+            break;
+        const int end = min(h + chunk, n_in);
+        int i = h;
+        while (i < end) {
+            // the run of records [i, i + cnt) that belong to one instance
+            const int idx = i + tid;
+            const bool v = idx < end;
+            Rec<W> r;
+            if (v)
+                r = load_rec<W>(a, frontier, n_act, n_front, act_list, in, idx);
+            if (tid == 0) {
+                s_inst = r.inst;
+                s_first = nthr;
+            }
+            __syncthreads();
+            const unsigned inst0 = s_inst;
+            if (!(v && r.inst == inst0))
+                atomicMin(&s_first, tid);
+            __syncthreads();
+            const int cnt = s_first;
+            const unsigned long long left = a.cnt.budget_left[inst0];
+            const bool budgeted = left != ~0ull;
+            if (tid == 0)
+                s_flag = (budgeted || first_only) && *(volatile unsigned *)&a.cnt.aborted[inst0];
+            __syncthreads();
+            const bool dropped = s_flag != 0;
+            if (tid < cnt && !dropped)
+                stk.put(tid, r.b, sm_from_rec<W>(r.meta), r.origin);
+            int top = dropped ? 0 : cnt;
+            if (inst0 != acc_inst) {
+                publish();
+                acc_inst = inst0;
+            }
+            __syncthreads();
+            unsigned long long nodes = 0, flushed = 0;
+            while (top > 0) {
+                const int n = min(nthr, top);
+                if (top + 3 * n > SB) {
+                    // room for 4n children: the oldest entries go to the next
+                    // pass, the rest move down (afterwards top <= max(n, SB/2),
+                    // so top + 3n <= SB for SB >= 6 blockDim)
+                    const int k = min(top - n, SB / 2);
+                    if (tid == 0)
+                        atomicAdd(&a.ctrl->spills, 1ull);
+                    hand_back(0, k, inst0);
+                    __syncthreads();
+                    for (int j0 = 0; j0 < top - k; j0 += nthr) {
+                        const int j = j0 + tid;
+                        const bool ok = j < top - k;
+                        B bb = 0;
+                        uint32_t mm = 0, oo = 0;
+                        if (ok)
+                            stk.get(k + j, bb, mm, oo);
+                        __syncthreads();
+                        if (ok)
+                            stk.put(j, bb, mm, oo);
+                        __syncthreads();
+                    }
+                    top -= k;
+                }
+                const bool act = tid < n;
+                B b = 0;
+                uint32_t mt = 0, org = 0;
+                if (act)
+                    stk.get(top - n + tid, b, mt, org);
+                top -= n;
+                nodes += (unsigned long long)n;
+                __syncthreads();
+                const bool goal = act && (b == GOAL);
+                const unsigned gmask = __ballot_sync(FULL, goal);
+                if (gmask) {
+                    const unsigned o = warp_min_u32(goal ? org : 0xffffffffu);
+                    if (lane == 0) {
+                        atomicAdd(&a.cnt.goals[inst0], (unsigned long long)__popc(gmask));
+                        atomicMin(&a.cnt.goal_origin[inst0], o);
+                        if (first_only)
+                            atomicOr(&a.cnt.aborted[inst0], ABORT_FOUND);
+                    }
+                }
+                const uint32_t sh_p = mt & 127u;
+                const int s = (int)((mt >> 11) & 255u);
+                const unsigned allowed = (act && !goal) ? (LegalMoves<W>::at_sh(sh_p) & ~((mt >> 7) & 15u)) : 0u;
+                const bool low = s < 2;
+                const LutRow<W> row = lut_row_sh<W>(lut, sh_p);
+                unsigned push4 = 0;
+                bool pruned = false;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const bool legal = (allowed >> m) & 1u;
+                    const unsigned t = BoardOps<W>::tile(b, sh_p + (uint32_t)(BITS * move_off<W>(m)));
+                    const bool away = away_bit<W>(row, m, t);
+                    push4 |= (legal && !(away && low)) ? (1u << m) : 0u;
+                    pruned |= legal && away && low;
+                }
+                if (pruned)
+                    fmin = min(fmin, 2 - s);
+                // slots: the block-wide prefix of the per-thread child counts
+                const unsigned c = __popc(push4);
+                const unsigned B0 = __ballot_sync(FULL, c & 1u), B1 = __ballot_sync(FULL, c & 2u),
+                               B2 = __ballot_sync(FULL, c & 4u);
+                const int off = __popc(B0 & lt) + 2 * __popc(B1 & lt) + 4 * __popc(B2 & lt);
+                if (lane == 0)
+                    s_cnt[warp] = __popc(B0) + 2 * __popc(B1) + 4 * __popc(B2);
+                __syncthreads();
+                int before = 0, total = 0;
+                for (int w = 0; w < nw; ++w) {
+                    const int x = s_cnt[w];
+                    before += w < warp ? x : 0;
+                    total += x;
+                }
+                int sp = top + before + off;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    if ((push4 >> m) & 1u) {
+                        const uint32_t sh_np = sh_p + (uint32_t)(BITS * move_off<W>(m));
+                        const unsigned t = BoardOps<W>::tile(b, sh_np);
+                        const bool away = away_bit<W>(row, m, t);
+                        const B child = BoardOps<W>::flip(b, t * move_mul<W>(m), (m < 2) ? sh_np : sh_p);
+                        const uint32_t cm =
+                            (sh_np + (mt & (255u << 11)) + ((1u << (3 - m)) << 7)) - (away ? (2u << 11) : 0u);
+                        stk.put(sp, child, cm, org);
+                        ++sp;
+                    }
+                }
+                top += total;
+                __syncthreads();
+
+                if (((++rounds) & 31) == 0) {
+                    // 1: first solution found, 2: over the node budget, 3: hand back
+                    if (tid == 0) {
+                        int f = 0;
+                        if (first_only && (*(volatile unsigned *)&a.cnt.aborted[inst0] & ABORT_FOUND))
+                            f = 1;
+                        if (!f && budgeted) {
+                            const unsigned long long before_n = atomicAdd(&a.cnt.search_nodes[inst0], nodes - flushed);
+                            if (before_n + (nodes - flushed) > left) {
+                                atomicOr(&a.cnt.aborted[inst0], ABORT_BUDGET);
+                                f = 2;
+                            }
+                        }
+                        if (!f && rounds >= a.tune.min_rounds &&
+                            *(volatile int *)&a.ctrl->exited >= a.tune.exit_threshold &&
+                            global_ns() - *(volatile unsigned long long *)&a.ctrl->t_start >=
+                                (unsigned long long)a.tune.min_pass_ns)
+                            f = 3;
+                        if (!f && rounds >= a.tune.min_rounds && slice_over(a))
+                            f = 3;
+                        s_flag = f;
+                    }
+                    if (budgeted)
+                        flushed = nodes;
+                    __syncthreads();
+                    const int f = s_flag;
+                    __syncthreads();
+                    if (f == 1 || f == 2) {
+                        top = 0;
+                        break;
+                    }
+                    if (f == 3) {
+                        stop = true;
+                        break;
+                    }
+                }
+            }
+            acc_nodes += nodes - flushed;
+            tot_nodes += nodes;
+            if (budgeted)
+                publish();
+            if (stop) {
+                hand_back(0, top, inst0);
+                hand_back_input(i + cnt, end);
+                // input no block has taken yet goes back too
+                for (;;) {
+                    if (tid == 0)
+                        s_h = atomicAdd(&a.ctrl->head, chunk);
+                    __syncthreads();
+                    const int h2 = s_h;
+                    __syncthreads();
+                    if (h2 >= n_in)
+                        break;
+                    hand_back_input(h2, min(h2 + chunk, n_in));
+                }
+                break;
+            }
+            i += cnt;
+        }
+        if (stop)
+            break;
+    }
+    publish();
+    if (tid == 0) {
+        if (!stop)
+            atomicAdd(&a.ctrl->exited, nw);
+        atomicMax(&a.ctrl->t_end, global_ns());
+        atomicAdd(&a.ctrl->search_nodes_total, tot_nodes);
+        __threadfence();
+        if (atomicAdd(&a.ctrl->done_warps, 1) == (int)gridDim.x - 1) {
+            __threadfence();
+            end_of_pass<W>(a);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------
 // The paper's BPIDA* kernel, kept as an ablation of the design above
 // (Algorithm 1 as printed): a block is one warp; each repetition pops
 // #threads / #actions = 8 nodes and lane i applies action (i mod 4) to node

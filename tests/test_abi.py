@@ -51,7 +51,7 @@ def test_variant_arguments_are_checked_before_any_work(lib):
     """Unknown variants, and the ablation variants 2-5 with a 24-puzzle
     width, first-solution mode or a node budget, are rejected on the host."""
     b = bpida.load()
-    bad = [dict(variant=6), dict(variant=-1), dict(variant=bpida.PSIMPLE, width=5),
+    bad = [dict(variant=7), dict(variant=-1), dict(variant=bpida.BLOCK_MODE, width=5), dict(variant=bpida.PSIMPLE, width=5),
            dict(variant=bpida.PSTATICLB, count_all=False), dict(variant=bpida.PFULLLB, node_budget=10),
            dict(variant=bpida.BPSTATIC, width=5), dict(variant=bpida.BPSTATIC, count_all=False)]
     for kw in bad:

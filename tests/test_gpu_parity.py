@@ -117,6 +117,8 @@ def test_all_8puzzle_states():
     dict(driver=1), dict(driver=1, split_target=1, stack_entries=1024),
     dict(min_pass_us=-1, exit_fraction_pct=1, min_rounds=32), dict(min_pass_us=1000),
     dict(variant=1), dict(variant=1, driver=1), dict(variant=1, split_target=1),
+    dict(variant=6), dict(variant=6, warps_per_block=8), dict(variant=6, warps_per_block=1, stack_entries=256),
+    dict(variant=6, driver=1, split_target=1), dict(variant=6, min_pass_us=-1, exit_fraction_pct=1, min_rounds=32),
 ])
 def test_tuning_knobs_do_not_change_results(cfg):
     insts = I.walks15_16x40()[:8]
@@ -307,6 +309,35 @@ def test_first_solution_mode():
         assert g["nodes"][:-1] == r.nodes[:-1] == f.nodes[:-1]
         assert 1 <= g["nodes"][-1] <= r.nodes[-1]
         assert len(g["moves"]) == g["length"]
+        assert P.replay(4, t, g["moves"]) == list(range(16))
+
+
+def test_block_mode_on_permutations_budgets_and_first_solutions():
+    """Block per subtree group (variant 6): the 40 cheapest random
+    permutations against the stored oracle results, a node budget that stops
+    one board in the middle of an iteration, and first-solution mode."""
+    doc = _golden("perms15_100")
+    cheap = sorted(doc["instances"], key=lambda r: sum(r["nodes"]))[:40]
+    perms = I.perms15_100()
+    insts = [perms[r["index"]] for r in cheap]
+    rc, got = gpu_solve(4, [x.tiles for x in insts], variant=6)
+    assert rc == bpida.OK
+    for r, g in zip(cheap, got):
+        assert g["length"] == r["length"] and g["nodes"] == r["nodes"] and g["solutions"] == r["solutions"]
+        assert "".join(map(str, g["moves"])) == r["moves"]
+    x = I.walks15_16x40()[6]
+    ref = oracle.solve(4, x.tiles)
+    mid = sum(ref.nodes[:-1]) + ref.nodes[-1] // 3
+    rc, got = gpu_solve(4, [x.tiles], variant=6, node_budget=mid)
+    assert got[0]["status"] == bpida.EBUDGET and got[0]["nodes"] == ref.nodes[:-1]
+    rc, got = gpu_solve(4, [x.tiles], variant=6, node_budget=ref.total_nodes)
+    assert got[0]["status"] == bpida.OK and got[0]["nodes"] == ref.nodes
+    tiles = [x.tiles for x in insts[:12]]
+    rc, got = gpu_solve(4, tiles, variant=6, count_all=False)
+    full = oracle.solve_batch(4, np.array(tiles, dtype=np.uint8))
+    for t, g, r in zip(tiles, got, full):
+        assert g["status"] == 0 and g["length"] == r.length and g["nodes"][:-1] == r.nodes[:-1]
+        assert 1 <= g["nodes"][-1] <= r.nodes[-1]
         assert P.replay(4, t, g["moves"]) == list(range(16))
 
 
