@@ -65,19 +65,18 @@ WORKLOAD_DESC = {
 # launches), its share on the integer ALU pipe (16 lanes per scheduler: one
 # warp instruction every 2 cycles, so above one half the ALU pipe, not issue,
 # bounds the kernel at issue peak / (2 x share)), and DRAM bytes (read +
-# write) per launch, for the kernel each form runs.
-#   batched: k_search<4,512,0>, steady-state launches of a batched solve
-#   (profiles/k_search_15puzzle_batched_pipe_mix.txt);
-#   plain: the fused-iteration variant k_search<4,512,1>, the final iteration
-#   of board 0 of perms15_100 as one pass
-#   (profiles/k_search_15puzzle_perms15_board0_final_iteration.txt), and over
-#   every launch of a plain solve of that board, ramp-up and short passes
-#   included (profiles/k_search_15puzzle_plain_solve_all_launches.txt).
+# write) of a captured launch, for the kernel each form runs.
+#   batched: k_search<4,480,0>, every launch of two batched solves of the
+#   4096-board mix; ALU share and DRAM bytes from one full capture
+#   (profiles/k_search_15puzzle_mixed15_4096_batched.txt);
+#   plain: the fused-iteration variant k_search<4,480,1>, the final iteration
+#   of board 0 of the mix as one pass
+#   (profiles/k_search_15puzzle_plain_fused_final_iteration.txt).
 KERNEL_COUNTERS = {
-    "batched": {"kernel": "k_search<4,512,0>", "instr_per_expansion": 5.53, "alu_pipe_share": 0.537,
-                "traffic_per_launch": None},
-    "plain": {"kernel": "k_search<4,512,1>", "instr_per_expansion": 5.86, "alu_pipe_share": 0.537,
-              "traffic_per_launch": 1745542, "instr_per_expansion_all_launches": 7.65},
+    "batched": {"kernel": "k_search<4,480,0>", "instr_per_expansion": 4.97, "alu_pipe_share": 0.415,
+                "traffic_per_launch": 9552128},
+    "plain": {"kernel": "k_search<4,480,1>", "instr_per_expansion": 5.32, "alu_pipe_share": 0.424,
+              "traffic_per_launch": None},
 }
 
 
@@ -898,10 +897,10 @@ def leg_perms(bpida, torch, dev, timer, steps, clocks_hint):
             "roofline_plain": kernel_roofline(bpida, torch, dev, boards, "plain", clocks_hint)}
 
 
-# 24-puzzle search kernel k_search<5,512,0>: warp instructions per expansion
-# of the final iteration of walk 406 of walks24_1024 (39.7M nodes, one pass,
-# ncu smsp__inst_executed.sum / nodes).
-KERNEL_COUNTERS_W5 = {"kernel": "k_search<5,512,0>", "instr_per_expansion": 10.2, "alu_pipe_share": 0.5,
+# 24-puzzle search kernel k_search<5,384,0>: warp instructions per expansion
+# and ALU share of the final iteration of walk 406 of walks24_1024 (39.7M
+# nodes, one pass) (profiles/k_search_24puzzle_walk406_final_iteration.txt).
+KERNEL_COUNTERS_W5 = {"kernel": "k_search<5,384,0>", "instr_per_expansion": 10.07, "alu_pipe_share": 0.559,
                       "traffic_per_launch": None}
 
 
