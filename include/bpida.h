@@ -225,10 +225,9 @@ bpida_status bpida_solve_ex(const bpida_config *cfg, const uint64_t *boards, int
 /*
  * bpida_solve_noalloc — the 15-puzzle solve without any device allocation.
  * The paper has no counterpart: it serves callers that cannot call
- * cudaMalloc when they want a solve (work issued while another part of the
- * program captures a CUDA graph, a device whose memory a framework pool has
- * already reserved, loops that cannot take cudaMalloc's implicit device
- * synchronisation).
+ * cudaMalloc when they want a solve (a device whose memory a framework's
+ * pool allocator has already reserved, loops that cannot take cudaMalloc's
+ * implicit device synchronisation).
  *   Same arguments and results as bpida_solve_ex with the default
  *   configuration (width 4, count_all = 1): boards, out_len, out_moves
  *   (n * bpida_max_len(4) bytes), out_nodes_per_iter (n * bpida_max_iters(4)
@@ -240,13 +239,14 @@ bpida_status bpida_solve_ex(const bpida_config *cfg, const uint64_t *boards, int
  *   BPIDA_NOALLOC_SCRATCH_BYTES held by every GPU that loads the library
  *   until the process exits. The first call on a device looks up the
  *   array's device address (cudaGetSymbolAddress) with that device current;
- *   make that first call before any stream capture begins. No call
- *   allocates or frees memory. Calls share the array: each call
- *   re-initialises what it reads, and calls that overlapped on the GPU would
- *   race (calls are serialised by a lock and synchronise `stream` before
- *   returning). The search runs with one two-warp block per SM, so it is
- *   slower than bpida_solve_ex; a hand-back overflow of its fixed queue
- *   returns BPIDA_ENOMEM.
+ *   after a cudaDeviceReset, call bpida_release_workspace() (which forgets
+ *   the address) before the next call. No call allocates or frees memory.
+ *   Calls share the array: each call re-initialises what it reads, and calls
+ *   that overlapped on the GPU would race (calls are serialised by a lock
+ *   and synchronise `stream` before returning). The search runs with one
+ *   two-warp block per SM, so it is slower than bpida_solve_ex; a hand-back
+ *   overflow of its fixed queue (2^18 records per pass) returns
+ *   BPIDA_ENOMEM.
  */
 #define BPIDA_NOALLOC_MAX_BOARDS 256
 #define BPIDA_NOALLOC_SCRATCH_BYTES (16u << 20)
@@ -334,7 +334,8 @@ void bpida_get_stats(bpida_stats *out);
  * (8e6). Process-wide; takes effect at the next call. */
 void bpida_set_fuse_nodes(uint64_t nodes);
 
-/* Free the calling device's workspace. */
+/* Free the calling device's workspaces (after waiting for their last calls)
+ * and forget bpida_solve_noalloc's array address on it. */
 void bpida_release_workspace(void);
 
 /* ---- pattern-database heuristic ----

@@ -40,6 +40,10 @@
 
 using namespace bp;
 
+namespace bp {
+void noalloc_forget(int dev);  // bpida_noalloc.cu
+}
+
 namespace {
 
 thread_local bpida_stats g_stats;
@@ -832,6 +836,7 @@ void bpida_release_workspace(void)
             w->release();
     g_last.ws = nullptr;
     tp::release(dev);
+    noalloc_forget(dev);
 }
 
 const char *bpida_status_str(int s)

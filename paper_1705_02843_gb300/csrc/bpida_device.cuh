@@ -1102,7 +1102,6 @@ __global__ void k_search(const Dev<W> a)
                     const uint32_t low4 = (mq & 0x7E00u) ? 0u : FM_BIT7;  // slack < 2
                     const uint32_t push4 = allowed4 & ~(away4 & low4);
                     prn |= allowed4 & away4 & low4;
-                    const uint32_t sh_p = (mq & 15u) << 2;
                     const uint32_t keep = mq & 0x7F0Fu;  // blank position and slack
                     // slots: this lane's children go to sp, sp + 1, ... (the
                     // prefix of the per-lane counts, from their bit-sliced ballots)

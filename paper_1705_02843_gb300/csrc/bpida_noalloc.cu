@@ -2,22 +2,20 @@
 // device memory.
 //
 // Some callers must not call cudaMalloc (or any allocating routine) at the
-// moment they want a solve: code that runs while another part of the
-// program captures work into a CUDA graph (allocation is not permitted
-// during a global-mode capture), hosts whose device memory is entirely
-// reserved up front by a framework's pool allocator, and latency-critical
-// loops that cannot afford cudaMalloc's implicit device synchronisation.
-// This entry point serves them: it runs the same kernels as bpida_solve_ex,
-// driven from the host, with its whole workspace taken from one file-scope
-// __device__ array of BPIDA_NOALLOC_SCRATCH_BYTES. It never calls
-// cudaMalloc, cudaFree, cudaMallocHost, a graph instantiation or an event
-// creation. The caller still passes device buffers for the boards and all
-// outputs.
+// moment they want a solve: hosts whose device memory is entirely reserved
+// up front by a framework's pool allocator, and latency-critical loops that
+// cannot afford cudaMalloc's implicit device synchronisation. This entry
+// point serves them: it runs the same kernels as bpida_solve_ex, driven from
+// the host, with its whole workspace taken from one file-scope __device__
+// array of BPIDA_NOALLOC_SCRATCH_BYTES. It never calls cudaMalloc, cudaFree,
+// cudaMallocHost, a graph instantiation or an event creation. The caller
+// still passes device buffers for the boards and all outputs.
 //
 // The array belongs to every GPU that loads this library, for the life of
 // the process. Its device address is taken once per device, on the first
-// call made with that device current (cudaGetSymbolAddress), so that first
-// call should come before any stream capture begins. Every call shares the
+// call made with that device current (cudaGetSymbolAddress); a
+// cudaDeviceReset makes that address stale, and bpida_release_workspace()
+// forgets it so that the next call takes it again. Every call shares the
 // array and leaves its contents behind; each call re-initialises everything
 // it reads (control block, instance state, counters) before use. Calls that
 // overlap on the GPU would race on the array; calls through this entry point
@@ -76,6 +74,16 @@ unsigned char *g_na_base[NA_MAX_DEVICES] = {};
     } while (0)
 
 }  // namespace
+
+namespace bp {
+// Forgets the array's device address on device dev (bpida_release_workspace).
+void noalloc_forget(int dev)
+{
+    std::lock_guard<std::mutex> lock(g_na_mu);
+    if (dev >= 0 && dev < NA_MAX_DEVICES)
+        g_na_base[dev] = nullptr;
+}
+}  // namespace bp
 
 extern "C" bpida_status bpida_solve_noalloc(const uint64_t *boards, int n, int *out_len, uint8_t *out_moves,
                                             uint64_t *out_nodes_per_iter, int *out_num_iters,
