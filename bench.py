@@ -164,6 +164,36 @@ def max_over_ranks(value, pg=None, device=None):
     return float(t.item())
 
 
+def shard_range(n, world, rank):
+    """The instance range [lo, hi) of one rank: n instances cut into world
+    contiguous ranges whose sizes differ by at most one."""
+    base, extra = divmod(n, world)
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
+def gather_rows(rows, pg=None, device=None):
+    """The final gather: every rank's result rows (its instance range, in
+    order) concatenated in rank order on every rank; the identity without a
+    process group."""
+    if pg is None:
+        return list(rows)
+    parts = [None] * pg.get_world_size()
+    pg.all_gather_object(parts, list(rows))
+    return [r for part in parts for r in part]
+
+
+def sum_over_ranks(value, pg=None, device=None):
+    """Sum of an integer over the ranks (the identity without a process group)."""
+    if pg is None:
+        return int(value)
+    import torch
+
+    t = torch.tensor([int(value)], dtype=torch.int64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return int(t.item())
+
+
 def replica_throughput(units_per_rank, seconds_per_rank, world, pg=None, device=None):
     """Whole-job throughput of N independent replicas: every rank processes
     the same amount of work; the job takes as long as the slowest rank."""
@@ -1020,6 +1050,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="mixed15_4096", choices=["mixed15_4096", "perms15_100"])
+    ap.add_argument("--replicas", action="store_true",
+                    help="with several GPUs: every GPU solves the whole workload (weak scaling) instead of its "
+                         "instance range")
     ap.add_argument("--plain-steps", type=int, default=3,
                     help="timed steps of the plain form (one call per board; slower, so fewer)")
     ap.add_argument("--sub-steps", type=int, default=3, help="timed steps of each sub-workload")
@@ -1137,8 +1170,16 @@ def main():
                           "iters": h["iters"], "nodes": h["nodes"], "stats": st}), flush=True)
         return
 
-    n = len(insts)
     gold = load_golden(args.workload)
+    # Multi-GPU: the instances are independent, so each rank solves its own
+    # instance range with no collective on the data path; the results are
+    # gathered at the end (strong scaling: the whole job is the workload).
+    # --replicas: every rank solves the whole workload (weak scaling).
+    n_all = len(insts)
+    copies = world if (world > 1 and args.replicas) else 1
+    lo, hi = (0, n_all) if copies > 1 else shard_range(n_all, world, rank)
+    insts = insts[lo:hi]
+    n = len(insts)
     packed = I.packed_array(insts)
     boards = torch.from_numpy(packed.view(np.int64)).to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -1150,26 +1191,34 @@ def main():
     def mx(v):
         return max_over_ranks(v, pg, dev)
 
+    def job_rows(hosts):
+        # the final gather (outside the timed region): every board of the job, in order
+        return hosts if copies > 1 else gather_rows(hosts, pg, dev)
+
     # headline: the batched form, K timed steps
     with ClockSampler(local) as clk:
         ms_b, agg_b, bsols = timer.run(batched_step, k, args.warmup)
     clocks = clk.summary()
     hb = hosts_of(bsols)
-    exp_per_step = sum(sum(h["nodes"]) for h in hb)
-    par_b = parity(hb, gold) if gold else None
+    exp_rank = sum(sum(h["nodes"]) for h in hb)
+    exp_per_step = copies * sum_over_ranks(exp_rank, pg if copies == 1 else None, dev)
+    rows_b = job_rows(hb)
+    par_b = parity(rows_b, gold) if gold else None
     t_batch = mx(sum(ms_b)) / 1e3
-    value = world * exp_per_step * k / t_batch
-    inst_s = world * n * k / t_batch
+    n_job = copies * n_all
+    value = exp_per_step * k / t_batch
+    inst_s = n_job * k / t_batch
 
     # the plain form: one call per board, fewer timed steps
     kp = max(1, min(args.plain_steps, k))
     ms_p, _, psols = timer.run(plain_step, kp, 1)
     hp = hosts_of(psols)
-    if sum(sum(h["nodes"]) for h in hp) != exp_per_step:
+    if sum(sum(h["nodes"]) for h in hp) != exp_rank:
         raise RuntimeError("batched and plain expansions differ")
-    par_p = parity(hp, gold) if gold else None
+    rows_p = job_rows(hp)
+    par_p = parity(rows_p, gold) if gold else None
     t_plain = mx(sum(ms_p)) / 1e3
-    plain_inst_s = world * n * kp / t_plain
+    plain_inst_s = n_job * kp / t_plain
 
     # end to end through the host-buffer path: pinned boards copied in and
     # every result copied back inside the timed region (batched form)
@@ -1195,10 +1244,12 @@ def main():
         return [s], {}
 
     ms_e2e, _, _ = timer.run(e2e_step, k, 1)
-    if int(host_out["nodes"].numpy().view(np.uint64).sum()) != exp_per_step:
+    if int(host_out["nodes"].numpy().view(np.uint64).sum()) != exp_rank:
         raise RuntimeError("end-to-end expansions differ")
     t_e2e = mx(sum(ms_e2e)) / 1e3
-    e2e_value = world * exp_per_step * k / t_e2e
+    e2e_value = exp_per_step * k / t_e2e
+
+    launches_job = sum_over_ranks(sum(a["launches"] for a in agg_b), pg, dev)
 
     # roofline of the dominant kernel (the batched form's k_search)
     roof = kernel_roofline(bpida, torch, dev, boards, "batched", clocks)
@@ -1253,26 +1304,29 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": k,
             "warmup": args.warmup, "ms_per_step": t_batch * 1e3 / k, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "scaling": "weak" if (world == 1 or copies > 1) else "strong",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC[args.workload],
-                       "mode": "batched: all %d boards in one solve call" % n,
+                       "mode": "batched: each GPU's boards in one solve call",
                        "driver": args.driver,
-                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "parallelism": ("replicas: every GPU solves all %d boards" % n_all) if copies > 1 else
+                                      ("instance ranges: %d GPUs, %d-%d boards each, results gathered" % (
+                                          world, n_all // world, -(-n_all // world)) if world > 1 else "single GPU"),
                        "l2": "flushed between steps (256 MiB write)"},
             "instances_per_s": inst_s,
             "expansions_per_step": exp_per_step,
-            "plain": {"value": world * exp_per_step * kp / t_plain, "unit": UNIT, "instances_per_s": plain_inst_s,
+            "plain": {"value": exp_per_step * kp / t_plain, "unit": UNIT, "instances_per_s": plain_inst_s,
                       "ms_per_step": t_plain * 1e3 / kp, "steps": kp, "mode": "one solve call per board"},
             "batched_over_plain_instances_per_s": inst_s / plain_inst_s,
             "parity": {"batched": par_b, "plain": par_p,
                        "against": "tests/golden/%s.json: stored oracle results (length, nodes per iteration, "
                                   "first solution, solution count) of every board" % args.workload},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": t_e2e * 1e3 / k, "instances_per_s": world * n * k / t_e2e},
+                    "ms_per_step": t_e2e * 1e3 / k, "instances_per_s": n_job * k / t_e2e},
             "roofline": roof,
             "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                        "reasons": clocks["reasons"]},
-            "gpu_launches": sum(a["launches"] for a in agg_b),
+            "gpu_launches": launches_job,
             "hbm_frontier_queue": hbm,
             "cpu_baseline": cpu,
         }

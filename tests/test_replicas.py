@@ -1,6 +1,8 @@
-"""Multi-GPU runs are independent replicas (instances do not interact), so
-the only collective is the benchmark's max-over-ranks timing. Checked with two
-gloo ranks on the CPU."""
+"""Multi-GPU runs: instances do not interact, so each rank solves its own
+instance range with no collective on the data path, and the results are
+gathered at the end (or, with --replicas, every rank solves the whole
+workload). The bench's collectives are the max-over-ranks timing, sums of
+counts and the final gather. Checked with two gloo ranks on the CPU."""
 import os
 import socket
 
@@ -24,7 +26,11 @@ def _rank(rank, world, port, q):
     # rank r took (r + 1) seconds for the same 100 boards
     v = bench.replica_throughput(100, float(rank + 1), world, dist)
     m = bench.max_over_ranks(rank * 10.0, dist)
-    q.put((rank, v, m))
+    # instance ranges of 4097 boards, each rank's rows gathered in order
+    lo, hi = bench.shard_range(4097, world, rank)
+    rows = bench.gather_rows([{"index": i, "rank": rank} for i in range(lo, hi)], dist)
+    total = bench.sum_over_ranks(hi - lo, dist)
+    q.put((rank, v, m, (lo, hi), [r["index"] for r in rows], [r["rank"] for r in rows], total))
     dist.destroy_process_group()
 
 
@@ -40,8 +46,14 @@ def test_two_gloo_ranks_aggregate_like_the_bench():
         p.join(timeout=60)
         assert p.exitcode == 0
     # job throughput = 2 ranks x 100 boards / slowest rank's 2 s
-    assert [round(v, 6) for _, v, _ in out] == [100.0, 100.0]
-    assert [m for _, _, m in out] == [10.0, 10.0]
+    assert [round(o[1], 6) for o in out] == [100.0, 100.0]
+    assert [o[2] for o in out] == [10.0, 10.0]
+    # the ranges cover 0..4096 once, in order; every rank sees every row
+    assert [o[3] for o in out] == [(0, 2049), (2049, 4097)]
+    for o in out:
+        assert o[4] == list(range(4097))
+        assert o[5] == [0] * 2049 + [1] * 2048
+        assert o[6] == 4097
 
 
 def test_single_process_is_identity():
@@ -49,6 +61,19 @@ def test_single_process_is_identity():
 
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.replica_throughput(100, 2.0, 1) == 50.0
+    assert bench.shard_range(10, 1, 0) == (0, 10)
+    assert bench.gather_rows([1, 2]) == [1, 2] and bench.sum_over_ranks(7) == 7
+
+
+@pytest.mark.parametrize("n,world", [(4096, 8), (4096, 3), (5, 8), (100, 7)])
+def test_instance_ranges_partition_the_workload(n, world):
+    import bench
+
+    rs = [bench.shard_range(n, world, r) for r in range(world)]
+    assert rs[0][0] == 0 and rs[-1][1] == n
+    assert all(a[1] == b[0] for a, b in zip(rs, rs[1:]))
+    sizes = [hi - lo for lo, hi in rs]
+    assert max(sizes) - min(sizes) <= 1
 
 
 def test_bench_pattern_database_constants_cover_every_partition():
