@@ -627,6 +627,7 @@ template <int W> struct WarpStack<W, false> {
     {
         e[i] = make_uint4((uint32_t)b, (uint32_t)(b >> 32), meta, org);
     }
+
     __device__ __forceinline__ void get(int i, uint64_t &b, uint32_t &meta, uint32_t &org) const
     {
         const uint4 v = e[i];
@@ -1053,7 +1054,10 @@ __global__ void k_search(const Dev<W> a)
                 const bool act = lane < n;
                 SB b = 0;
                 uint32_t mt = 0, org = 0;
-                if (act)
+                // the four-move step reads every lane's entry unconditionally (a
+                // lane past n reads an entry below S: lane < 32 <= S when n = top,
+                // and top - 1 otherwise) and ignores the lanes past n
+                if (FM || act)
                     stk.get(top - n + lane, b, mt, org);
                 top -= n;
                 nodes += (unsigned long long)n;
