@@ -73,9 +73,9 @@ WORKLOAD_DESC = {
 #   of board 0 of the mix as one pass
 #   (profiles/k_search_15puzzle_plain_fused_final_iteration.txt).
 KERNEL_COUNTERS = {
-    "batched": {"kernel": "k_search<4,480,0>", "instr_per_expansion": 4.97, "alu_pipe_share": 0.415,
-                "traffic_per_launch": 9552128},
-    "plain": {"kernel": "k_search<4,480,1>", "instr_per_expansion": 5.32, "alu_pipe_share": 0.424,
+    "batched": {"kernel": "k_search<4,480,0>", "instr_per_expansion": 4.75, "alu_pipe_share": 0.403,
+                "traffic_per_launch": 9604864},
+    "plain": {"kernel": "k_search<4,480,1>", "instr_per_expansion": 5.25, "alu_pipe_share": 0.404,
               "traffic_per_launch": None},
 }
 
@@ -930,7 +930,7 @@ def leg_perms(bpida, torch, dev, timer, steps, clocks_hint):
 # 24-puzzle search kernel k_search<5,384,0>: warp instructions per expansion
 # and ALU share of the final iteration of walk 406 of walks24_1024 (39.7M
 # nodes, one pass) (profiles/k_search_24puzzle_walk406_final_iteration.txt).
-KERNEL_COUNTERS_W5 = {"kernel": "k_search<5,384,0>", "instr_per_expansion": 10.07, "alu_pipe_share": 0.559,
+KERNEL_COUNTERS_W5 = {"kernel": "k_search<5,384,0>", "instr_per_expansion": 9.94, "alu_pipe_share": 0.556,
                       "traffic_per_launch": None}
 
 

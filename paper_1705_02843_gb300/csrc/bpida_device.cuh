@@ -1052,13 +1052,12 @@ __global__ void k_search(const Dev<W> a)
                 }
                 // pop: lane l takes entry top - n + l
                 const bool act = lane < n;
-                SB b = 0;
-                uint32_t mt = 0, org = 0;
-                // the four-move step reads every lane's entry unconditionally (a
-                // lane past n reads an entry below S: lane < 32 <= S when n = top,
-                // and top - 1 otherwise) and ignores the lanes past n
-                if (FM || act)
-                    stk.get(top - n + lane, b, mt, org);
+                SB b;
+                uint32_t mt, org;
+                // every lane reads an entry unconditionally (a lane past n reads an
+                // entry below S: lane < 32 <= S when n = top, and top - 1
+                // otherwise); the lanes past n push nothing and count nothing
+                stk.get(top - n + lane, b, mt, org);
                 top -= n;
                 nodes += (unsigned long long)n;
                 __syncwarp();
