@@ -569,17 +569,21 @@ __device__ __forceinline__ uint32_t rec_from_fm(uint32_t m)
     const uint32_t last = e ? 3u - (uint32_t)((__ffs((int)e) - 1) >> 3) : LAST_NONE;
     return m_make(m & 15u, last, (m >> 8) & 127u);
 }
-// Per blank position p, in shared memory: entry p (16 bytes)
-//   x: byte selector of the neighbours (up, left, right, down) in the board
-//      viewed as 8 bytes (an off-board neighbour selects byte 0)
-//   y: 0x0F in byte m when neighbour m's tile is the low nibble of its byte
-//   z: per byte m, 127 + the threshold of move m
-//   w: bit 8m + 7 set when move m keeps the blank on the board
-// and entries 16 + 2p, 17 + 2p: per move m, the low and high 32 bits of
-// 16^p + 16^(p + displacement of m) (0 for a move off the board).
+// Per blank position p, in shared memory, six arrays of 16 eight-byte
+// entries (a half-warp reads any 16 entries of one array without a bank
+// conflict):
+//   [p]      x: byte selector of the neighbours (up, left, right, down) in
+//               the board viewed as 8 bytes (an off-board neighbour selects
+//               byte 0); y: 0x0F in byte m when neighbour m's tile is the
+//               low nibble of its byte
+//   [16 + p] x: per byte m, 127 + the threshold of move m; y: bit 8m + 7 set
+//               when move m keeps the blank on the board
+//   [32 + p], [48 + p], [64 + p], [80 + p]: per move m, the low (moves 0-1,
+//               2-3) and high (moves 0-1, 2-3) 32-bit words of 16^p +
+//               16^(p + displacement of m) (0 for a move off the board).
 struct FourMoveTable {
     static constexpr int BYTES = 16 * 16 + 16 * 32;
-    __device__ static void load(uint4 *t)
+    __device__ static void load(uint2 *t)
     {
         for (int p = threadIdx.x; p < 16; p += blockDim.x) {
             const int r = p >> 2, c = p & 3;
@@ -596,15 +600,18 @@ struct FourMoveTable {
                 if (on[m])
                     legal |= 0x80u << (8 * m);
             }
-            t[p] = make_uint4(sel, lowm, z, legal);
             uint32_t lo[4], hi[4];
             for (int m = 0; m < 4; ++m) {
                 const uint64_t v = on[m] ? (1ull << (4 * p)) | (1ull << (4 * np[m])) : 0ull;
                 lo[m] = (uint32_t)v;
                 hi[m] = (uint32_t)(v >> 32);
             }
-            t[16 + 2 * p] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-            t[17 + 2 * p] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            t[p] = make_uint2(sel, lowm);
+            t[16 + p] = make_uint2(z, legal);
+            t[32 + p] = make_uint2(lo[0], lo[1]);
+            t[48 + p] = make_uint2(lo[2], lo[3]);
+            t[64 + p] = make_uint2(hi[0], hi[1]);
+            t[80 + p] = make_uint2(hi[2], hi[3]);
         }
     }
 };
@@ -871,7 +878,7 @@ __global__ void k_search(const Dev<W> a)
     }
     SharedLut<W>::load(lut, a.lut);
     if constexpr (FourMoves<W, PDB>::on)
-        FourMoveTable::load((uint4 *)(smem + SharedLut<W>::BYTES));
+        FourMoveTable::load((uint2 *)(smem + SharedLut<W>::BYTES));
     const PdbInfo *pi = nullptr;
     if constexpr (PDB) {
         static_assert(W <= 4, "pattern databases: 8- and 15-puzzle");
@@ -891,7 +898,7 @@ __global__ void k_search(const Dev<W> a)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Stack stk;
     stk.init(smem + SearchSmem<W, PDB>::TABLES + (size_t)warp * S * Stack::ENTRY_BYTES, S);
-    const uint4 *fmtab = (const uint4 *)(smem + SharedLut<W>::BYTES);
+    const uint2 *fmtab = (const uint2 *)(smem + SharedLut<W>::BYTES);
     // byte selectors and the slack step of the four-move children, read
     // from shared memory so that they stay multiplier operands
     __shared__ uint32_t s_one;
@@ -1094,7 +1101,9 @@ __global__ void k_search(const Dev<W> a)
                 if constexpr (FM) {
                     // the four moves at once (see FourMoves)
                     const uint32_t mq = mt;
-                    const uint4 e = fmtab[mq & 15u];
+                    const uint32_t p = mq & 15u;
+                    const uint2 e01 = fmtab[p], e23 = fmtab[16 + p];
+                    const uint4 e = make_uint4(e01.x, e01.y, e23.x, e23.y);
                     const uint64_t bq = (uint64_t)b;
                     const uint32_t G = __byte_perm((uint32_t)bq, (uint32_t)(bq >> 32), e.x);
                     // byte m's low nibble: the tile that move m slides into the blank
@@ -1112,7 +1121,7 @@ __global__ void k_search(const Dev<W> a)
                     const unsigned B0 = __ballot_sync(FULL, c & 1u), B1 = __ballot_sync(FULL, c & 2u),
                                    B2 = __ballot_sync(FULL, c & 4u);
                     int sp = base + __popc(B0 & lt) + 2 * __popc(B1 & lt) + 4 * __popc(B2 & lt);
-                    base += __popc(B0) + 2 * __popc(B1) + 4 * __popc(B2);
+                    base += (int)__reduce_add_sync(FULL, c);
                     // the children: move m XORs its tile t into the blank's field and
                     // the neighbour's field, i.e. adds t times a per-position
                     // constant to each 32-bit half (the fields never carry); the
@@ -1121,7 +1130,8 @@ __global__ void k_search(const Dev<W> a)
                     // pipe rather than on the integer ALU pipe, which the tests
                     // and the bit logic above already keep busy
                     const uint32_t Yc = Y & 0x0F0F0F0Fu;
-                    const uint4 ml = fmtab[16 + (mq & 15u) * 2], mh = fmtab[17 + (mq & 15u) * 2];
+                    const uint2 l01 = fmtab[32 + p], l23 = fmtab[48 + p], h01 = fmtab[64 + p], h23 = fmtab[80 + p];
+                    const uint4 ml = make_uint4(l01.x, l01.y, l23.x, l23.y), mh = make_uint4(h01.x, h01.y, h23.x, h23.y);
                     const uint32_t mlo[4] = {ml.x, ml.y, ml.z, ml.w}, mhi[4] = {mh.x, mh.y, mh.z, mh.w};
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
