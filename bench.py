@@ -73,9 +73,9 @@ WORKLOAD_DESC = {
 #   of board 0 of the mix as one pass
 #   (profiles/k_search_15puzzle_plain_fused_final_iteration.txt).
 KERNEL_COUNTERS = {
-    "batched": {"kernel": "k_search<4,480,0>", "instr_per_expansion": 4.75, "alu_pipe_share": 0.403,
-                "traffic_per_launch": 9604864},
-    "plain": {"kernel": "k_search<4,480,1>", "instr_per_expansion": 5.25, "alu_pipe_share": 0.404,
+    "batched": {"kernel": "k_search<4,480,0>", "instr_per_expansion": 4.78, "alu_pipe_share": 0.425,
+                "traffic_per_launch": 9683712},
+    "plain": {"kernel": "k_search<4,480,1>", "instr_per_expansion": 5.15, "alu_pipe_share": 0.418,
               "traffic_per_launch": None},
 }
 
