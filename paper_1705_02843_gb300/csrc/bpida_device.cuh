@@ -155,9 +155,16 @@ template <int W> struct SharedLut {
                 d[p] = v;
             }
         } else {
+            // bits 28..31 of the first word: the four legal bits again (bit
+            // 28 + m: move m), so that one shift gives the position's moves
+            // (tiles are at most 24: the away bits stay below)
             uint4 *d = (uint4 *)dst;
-            for (int p = threadIdx.x; p < Geo<W>::N; p += blockDim.x)
-                d[p] = make_uint4(src.e[p][0], src.e[p][1], src.e[p][2], src.e[p][3]);
+            for (int p = threadIdx.x; p < Geo<W>::N; p += blockDim.x) {
+                uint32_t legal = 0;
+                for (int m = 0; m < 4; ++m)
+                    legal |= (src.e[p][m] & 1u) << (28 + m);
+                d[p] = make_uint4(src.e[p][0] | legal, src.e[p][1], src.e[p][2], src.e[p][3]);
+            }
         }
     }
     __device__ static __forceinline__ LutRow<W> row(const unsigned char *base, int p)
@@ -615,6 +622,33 @@ struct FourMoveTable {
         }
     }
 };
+// ---- the 24-puzzle search step in the blank's frame ----
+// The 24-puzzle's search stacks hold each board turned so that the blank is
+// in field 0: field j holds the tile of cell (p + j) mod 25, p the blank's
+// cell (the 125 used bits rotated right by 5p). The four neighbours then sit
+// in fixed fields (up 20, left 24, right 1, down 5), and sliding the tile t
+// of field j into the blank gives the child in its own blank's frame as the
+// parent turned by a fixed amount:
+//   child = rotr(R, 5j) ^ t ^ (t << 5(25 - j))
+// (field 0 turns from t to the blank; field 25 - j, the parent's blank cell,
+// gets t). Every shift has a constant amount, where the board's own frame
+// needs a 128-bit shift by the blank's position per tile read and per child.
+// Records (queues, frontiers) keep the board's own frame; the stack entry's
+// metadata is the same in both.
+template <int W, bool PDB> struct BlankFrame {
+    static constexpr bool on = W == 5 && !PDB;
+};
+static constexpr u128 BOARD125 = (((u128)1) << 125) - 1u;
+// sh = 5p, the blank's field offset (0 <= sh < 125)
+__device__ __forceinline__ u128 to_blank_frame(u128 b, uint32_t sh)
+{
+    return sh ? (((b >> sh) | (b << (125u - sh))) & BOARD125) : b;
+}
+__device__ __forceinline__ u128 from_blank_frame(u128 r, uint32_t sh)
+{
+    return sh ? (((r << sh) | (r >> (125u - sh))) & BOARD125) : r;
+}
+
 // Shared memory of the search kernel before the warp stacks.
 template <int W, bool PDB = false> struct SearchSmem {
     static constexpr int TABLES = SharedLut<W>::BYTES + (FourMoves<W, PDB>::on ? FourMoveTable::BYTES : 0);
@@ -749,7 +783,7 @@ template <int W> __device__ __forceinline__ LutRow<W> lut_row_sh(const unsigned 
 template <int W, int S, bool PDB = false, typename Stack = WarpStack<W>>
 __device__ __forceinline__ void hand_back_stack(const Dev<W> &a, Rec<W> *out, const Stack &stk,
                                                 int from, int k, unsigned inst, int lane,
-                                                const PdbInfo *pi = nullptr, bool fm = false)
+                                                const PdbInfo *pi = nullptr, bool fm = false, bool bf = false)
 {
     if (k <= 0)
         return;
@@ -769,6 +803,8 @@ __device__ __forceinline__ void hand_back_stack(const Dev<W> &a, Rec<W> *out, co
         Rec<W> r;
         if constexpr (PDB)
             r.b = pdb_board<W>((uint64_t)(b >> 64), *pi);
+        else if constexpr (W == 5)
+            r.b = bf ? from_blank_frame(b, m & 127u) : b;
         else
             r.b = b;
         r.meta = fm ? rec_from_fm(m) : rec_from_sm<W>(m);
@@ -863,6 +899,7 @@ __global__ void k_search(const Dev<W> a)
     typedef WarpStack<W, (W == 5) || PDB> Stack;
     constexpr int BITS = Geo<W>::BITS;
     constexpr bool FM = FourMoves<W, PDB>::on;           // four moves at once (15-puzzle)
+    constexpr bool BF = BlankFrame<W, PDB>::on;          // boards in the blank's frame (24-puzzle)
     extern __shared__ __align__(16) unsigned char smem[];
     // end-of-pass bookkeeping is combined per block, so that the grid-wide
     // counters see one atomic per block instead of one per warp
@@ -993,6 +1030,9 @@ __global__ void k_search(const Dev<W> a)
                     uint32_t vb;
                     pdb_h(a.pdb, *pi, (uint64_t)(e >> 64), &vb);
                     stk.put(lane, e, sm_from_rec<W>(r.meta) | vb, r.origin);
+                } else if constexpr (BF) {
+                    const uint32_t sm = sm_from_rec<W>(r.meta);
+                    stk.put(lane, to_blank_frame(r.b, sm & 127u), sm, r.origin);
                 } else {
                     stk.put(lane, r.b, FM ? fm_from_rec(r.meta) : sm_from_rec<W>(r.meta), r.origin);
                 }
@@ -1040,7 +1080,7 @@ __global__ void k_search(const Dev<W> a)
                         }
                         ovf_n += k;
                     } else {
-                        hand_back_stack<W, S, PDB>(a, out, stk, 0, k, inst0, lane, pi, FM);
+                        hand_back_stack<W, S, PDB>(a, out, stk, 0, k, inst0, lane, pi, FM, BF);
                     }
                     __syncwarp();
                     for (int j0 = 0; j0 < top - k; j0 += 32) {
@@ -1069,7 +1109,9 @@ __global__ void k_search(const Dev<W> a)
                 nodes += (unsigned long long)n;
                 __syncwarp();
 
-                const bool goal = act && (b == GOAL);
+                // (in the blank's frame, a board whose blank is elsewhere can
+                // read as the goal)
+                const bool goal = act && (b == GOAL) && (!BF || (mt & 127u) == 0u);
                 const unsigned gmask = __ballot_sync(FULL, goal);
                 if (gmask) {
                     const unsigned o = warp_min_u32(goal ? org : 0xffffffffu);
@@ -1148,6 +1190,75 @@ __global__ void k_search(const Dev<W> a)
                         }
                     }
 
+                } else if constexpr (BF) {
+                    // the 24-puzzle in the blank's frame (see BlankFrame): the
+                    // position's table row gives the legal moves (bits 28..31
+                    // of word 0) and, word m, whether move m's tile slides away
+                    // from its goal cell (bit t)
+                    const uint32_t sh_p = mt & 127u;
+                    const LutRow<W> row = lut_row_sh<W>(lut, sh_p);
+                    const uint32_t rw[4] = {row.v.x, row.v.y, row.v.z, row.v.w};
+                    const uint32_t w0 = (uint32_t)b, w1 = (uint32_t)(b >> 32), w2 = (uint32_t)(b >> 64),
+                                   w3 = (uint32_t)(b >> 96);
+                    // the tiles of the neighbours up, left, right, down (fields 20, 24, 1, 5)
+                    const uint32_t t[4] = {(w3 >> 4) & 31u, w3 >> 24, (w0 >> 5) & 31u, (w0 >> 25) & 31u};
+                    // moves other than the inverse of the parent's (bits 7..10 of mt)
+                    const uint32_t ok4 = (act && !goal) ? ((rw[0] >> 28) & ~(mt >> 7) & 15u) : 0u;
+                    uint32_t aw[4];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        aw[m] = (rw[m] >> t[m]) & 1u;
+                    const uint32_t away4 = aw[0] + 2u * aw[1] + 4u * aw[2] + 8u * aw[3];
+                    const uint32_t cut4 = (s < 2) ? (ok4 & away4) : 0u;  // children past the limit
+                    const uint32_t push4 = ok4 & ~cut4;
+                    if (cut4)
+                        fmin = min(fmin, 2 - s);
+                    // slots: this lane's children go to sp, sp + 1, ... (the
+                    // prefix of the per-lane counts, from their bit-sliced ballots)
+                    const unsigned c = __popc(push4);
+                    const unsigned B0 = __ballot_sync(FULL, c & 1u), B1 = __ballot_sync(FULL, c & 2u),
+                                   B2 = __ballot_sync(FULL, c & 4u);
+                    int sp = base + __popc(B0 & lt) + 2 * __popc(B1 & lt) + 4 * __popc(B2 & lt);
+                    base += (int)__reduce_add_sync(FULL, c);
+                    // the children: the board turned left by 25 (up) or 5 bits
+                    // (left), right by 5 (right) or 25 (down); field 0 then holds
+                    // the tile (it becomes the blank: subtract it) and the
+                    // parent's blank cell, now field 5, 1, 24 or 20, holds 0 (it
+                    // gets the tile: add it). A left turn also brings the low 3
+                    // bits of the tile's old field to bits 125..127 (subtract
+                    // them); a right turn wraps field 0, which is zero. Every
+                    // field update is thus one multiply-add.
+                    const uint32_t w3s = w3 << 3;  // field 24 at the top of a word
+                    uint32_t c0[4], c1[4], c2[4], c3[4];
+                    c0[0] = __funnelshift_l(w3s, w0, 25) + t[0] * ((1u << 25) - 1u);
+                    c1[0] = __funnelshift_l(w0, w1, 25);
+                    c2[0] = __funnelshift_l(w1, w2, 25);
+                    c3[0] = __funnelshift_l(w2, w3, 25) - t[0] * (1u << 29);
+                    c0[1] = __funnelshift_l(w3s, w0, 5) + t[1] * 31u;
+                    c1[1] = __funnelshift_l(w0, w1, 5);
+                    c2[1] = __funnelshift_l(w1, w2, 5);
+                    c3[1] = __funnelshift_l(w2, w3, 5) - t[1] * (1u << 29);
+                    c0[2] = __funnelshift_r(w0, w1, 5) - t[2];
+                    c1[2] = __funnelshift_r(w1, w2, 5);
+                    c2[2] = __funnelshift_r(w2, w3, 5);
+                    c3[2] = (w3 >> 5) + t[2] * (1u << 24);
+                    c0[3] = __funnelshift_r(w0, w1, 25) - t[3];
+                    c1[3] = __funnelshift_r(w1, w2, 25);
+                    c2[3] = __funnelshift_r(w2, w3, 25);
+                    c3[3] = (w3 >> 25) + ((w0 & 0x01FFFFFFu) | t[3]) * 16u;
+                    // the child's blank, its excluded move (the inverse of m) and
+                    // its slack (s - 2 when the tile moved away, else s)
+                    const uint32_t keep = mt & ~(15u << 7);
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        if ((push4 >> m) & 1u) {
+                            const uint32_t cm = aw[m] * (0u - (2u << 11)) +
+                                                (keep + (uint32_t)(BITS * move_off<W>(m)) + ((1u << (3 - m)) << 7));
+                            const B child = ((u128)c3[m] << 96) | ((u128)c2[m] << 64) | ((u128)c1[m] << 32) | c0[m];
+                            stk.put(sp, child, cm, org);
+                            ++sp;
+                        }
+                    }
                 } else {
                 const uint32_t sh_p = mt & 127u;
                 const unsigned allowed =
@@ -1281,9 +1392,9 @@ __global__ void k_search(const Dev<W> a)
             if (budgeted)
                 publish();
             if (stop) {
-                hand_back_stack<W, S, PDB>(a, out, stk, 0, top, inst0, lane, pi, FM);
+                hand_back_stack<W, S, PDB>(a, out, stk, 0, top, inst0, lane, pi, FM, BF);
                 if (OVF)
-                    hand_back_stack<W, S, PDB>(a, out, ovf, 0, ovf_n, inst0, lane, pi, FM);
+                    hand_back_stack<W, S, PDB>(a, out, ovf, 0, ovf_n, inst0, lane, pi, FM, BF);
                 ovf_n = 0;
                 hand_back_records<W>(a, frontier, n_act, n_front, act, in, out, i + cnt, end, lane);
                 // input that no warp has taken yet goes back too (a stop at

@@ -205,6 +205,27 @@ def test_24puzzle_walks():
     check_against(5, tiles, got, oracle.solve_batch(5, np.array(tiles, dtype=np.uint8)))
 
 
+@pytest.mark.parametrize("cfg", [
+    dict(exit_fraction_pct=1, min_rounds=1),
+    dict(exit_fraction_pct=1, min_rounds=1, split_target=8, warps_per_block=4),
+    dict(exit_fraction_pct=5, min_rounds=16, split_target=64, stack_entries=512),
+])
+def test_24puzzle_hand_backs(cfg):
+    """24-puzzle batches with busy warps handing their stacks back early
+    and often (many passes per step): open nodes leave the search stacks as
+    records and come back, so the stack's board form is converted both ways
+    many times. Results against the oracle; the host driver reports the
+    passes."""
+    insts = [I.make_walk(5, 930 + s, 36 + 2 * s) for s in range(10)]
+    tiles = [x.tiles for x in insts]
+    ref = oracle.solve_batch(5, np.array(tiles, dtype=np.uint8))
+    rc, got = gpu_solve(5, tiles, driver=1, **cfg)
+    assert rc == bpida.OK
+    st = bpida.last_stats()
+    assert st["passes"] > st["steps"]
+    check_against(5, tiles, got, ref)
+
+
 def _golden(name):
     path = os.path.join(GOLDEN, name + ".json")
     if not os.path.exists(path):
