@@ -607,11 +607,19 @@ struct FourMoveTable {
                 if (on[m])
                     legal |= 0x80u << (8 * m);
             }
+            // per 32-bit half: 16^p for the blank's field (it gets the tile)
+            // less 16^np for the neighbour's (it loses it), modulo 2^32
             uint32_t lo[4], hi[4];
             for (int m = 0; m < 4; ++m) {
-                const uint64_t v = on[m] ? (1ull << (4 * p)) | (1ull << (4 * np[m])) : 0ull;
-                lo[m] = (uint32_t)v;
-                hi[m] = (uint32_t)(v >> 32);
+                lo[m] = hi[m] = 0u;
+                if (!on[m])
+                    continue;
+                const int q[2] = {p, np[m]};
+                for (int k = 0; k < 2; ++k) {
+                    const uint32_t f = 1u << (4 * (q[k] & 7));
+                    uint32_t &h = q[k] < 8 ? lo[m] : hi[m];
+                    h = k == 0 ? h + f : h - f;
+                }
             }
             t[p] = make_uint2(sel, lowm);
             t[16 + p] = make_uint2(z, legal);
@@ -1164,9 +1172,10 @@ __global__ void k_search(const Dev<W> a)
                                    B2 = __ballot_sync(FULL, c & 4u);
                     int sp = base + __popc(B0 & lt) + 2 * __popc(B1 & lt) + 4 * __popc(B2 & lt);
                     base += (int)__reduce_add_sync(FULL, c);
-                    // the children: move m XORs its tile t into the blank's field and
-                    // the neighbour's field, i.e. adds t times a per-position
-                    // constant to each 32-bit half (the fields never carry); the
+                    // the children: move m writes its tile t into the blank's field
+                    // (zero) and clears the neighbour's (which holds t), i.e. adds t
+                    // times a per-position constant to each 32-bit half (16^p less
+                    // 16^np; a field never carries or borrows), one multiply-add; the
                     // tile and the away bit of byte m are read with byte dot
                     // products, so the step's arithmetic runs on the multiply-add
                     // pipe rather than on the integer ALU pipe, which the tests
@@ -1178,7 +1187,7 @@ __global__ void k_search(const Dev<W> a)
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
                         const uint32_t t = (uint32_t)__dp4a(Yc, ebyte[m], 0u);
-                        const uint32_t clo = (uint32_t)bq ^ (t * mlo[m]), chi = (uint32_t)(bq >> 32) ^ (t * mhi[m]);
+                        const uint32_t clo = t * mlo[m] + (uint32_t)bq, chi = t * mhi[m] + (uint32_t)(bq >> 32);
                         const B child = ((uint64_t)chi << 32) | clo;
                         // the child's blank, its excluded move (the inverse of m)
                         // and its slack (s - 2 when the tile moved away, else s)
