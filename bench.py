@@ -258,7 +258,7 @@ def run_serving(args):
     for rate in rates:
         n_req = int(min(args.serving_max_requests, rate * args.serving_seconds))
         summary, results, insts = serve(bpida, rate, n_req, args.serving_slice_us)
-        summary["parity"] = check_served(bpida, torch, dev, results, insts)
+        summary["parity"], summary["batched_capacity"] = check_served(bpida, torch, dev, results, insts)
         out.append(summary)
         print(json.dumps(out[-1]), file=sys.stderr, flush=True)
     best = max(out, key=lambda r: r["completed_per_s"])
@@ -889,7 +889,13 @@ def check_served(bpida, torch, dev, results, insts):
     solve call (which the parity tests check against the oracle) and replays
     to the goal."""
     b = torch.from_numpy(I.packed_array(insts).view(np.int64)).to(dev)
-    ref = bpida.solve(b, 4).to_host()
+    bpida.solve(b, 4).synchronize()  # warm-up (the call's graph)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    sol = bpida.solve(b, 4)
+    e1.record()
+    ref = sol.to_host()
+    batched_s = e0.elapsed_time(e1) / 1e3
     bad = 0
     for i, x in enumerate(insts):
         r, h = results[i], ref[i]
@@ -898,7 +904,10 @@ def check_served(bpida, torch, dev, results, insts):
                 replay(4, x.tiles, r["moves"]) != list(range(16)):
             bad += 1
     return {"checked": len(insts), "mismatched": bad,
-            "against": "the same boards solved in one batched call, and a replay of every solution"}
+            "against": "the same boards solved in one batched call, and a replay of every solution"}, \
+        {"instances_per_s": len(insts) / batched_s, "ms": batched_s * 1e3,
+         "what": "the same requests' boards solved in one batched call (CUDA events): the GPU's throughput "
+                 "on this request mix, which bounds the service's completed requests/s"}
 
 
 def leg_perms(bpida, torch, dev, timer, steps, clocks_hint):
@@ -982,7 +991,7 @@ def leg_serving(bpida, torch, dev, rates, n_req):
     out = []
     for rate in rates:
         summary, results, insts = serve(bpida, rate, n_req)
-        summary["parity"] = check_served(bpida, torch, dev, results, insts)
+        summary["parity"], summary["batched_capacity"] = check_served(bpida, torch, dev, results, insts)
         out.append(summary)
     return {"workload": "Poisson arrivals; 98% walks of 30-90 moves, 2% random permutations; "
                         "latency from submit to pollable result", "mode": "continuous batching, 2 ms time slices",
@@ -1089,15 +1098,16 @@ def main():
                          "host launches every kernel (same kernels; ncu can list them)")
     ap.add_argument("--profile-case", type=int, default=None, metavar="IDX",
                     help="solve board IDX alone, twice, through the host-driven loop with one "
-                         "search pass per iteration (for ncu captures: the final iteration's "
-                         "k_search launch is number iters-1), print its statistics and exit")
+                         "search pass per step, print the first solve's search launches (duration, "
+                         "nodes) and statistics and exit (for ncu captures)")
     ap.add_argument("--profile-batched", action="store_true",
                     help="solve all boards of the workload in one call, twice, through the host-driven loop "
+                         "with one search pass per step, print the first solve's search launches and exit "
                          "(for ncu captures of the search kernel at full occupancy)")
     ap.add_argument("--profile-default", action="store_true",
-                    help="with --profile-case: keep the default hand-back (as in the bench)")
+                    help="with --profile-case or --profile-batched: keep the default hand-back (as in the bench)")
     ap.add_argument("--profile-width", type=int, default=4, choices=[4, 5],
-                    help="with --profile-case: 5 = a board of the 24-puzzle walk workload")
+                    help="with --profile-case or --profile-batched: 5 = the 24-puzzle walk workload")
     ap.add_argument("--profile-variant", type=int, default=0, metavar="V",
                     help="with --profile-case: solve with bpida_config.variant V (2-4: the thread-parallel "
                          "configurations; the final iteration's k_search_tp launch is number iters-1)")
@@ -1138,36 +1148,48 @@ def main():
         pg = dist
 
     insts = I.WORKLOADS[args.workload]()
-    if args.profile_batched:
-        b = torch.from_numpy(I.packed_array(insts).view(np.int64)).to(dev)
-        for rep in range(2):
-            s = bpida.solve(b, 4, bpida.make_config(4, driver=1))
-            torch.cuda.synchronize(dev)
-        print(json.dumps({"profile_batched": len(insts), "status": s.status,
-                          "nodes": int(s.nodes.cpu().numpy().view(np.uint64).sum()),
-                          "stats": bpida.last_stats()}), flush=True)
-        return
-    if args.profile_case is not None:
+    if args.profile_batched or args.profile_case is not None:
+        # for ncu: two solves through the host-driven loop (ncu cannot see
+        # kernels inside graphs that hold conditional nodes), by default with
+        # hand-back off (one search pass per step, plus passes for stack
+        # overflows: the launch sequence is the same in every run); the first
+        # solve's search launches are printed with their durations and node
+        # counts, so that a profiler's instruction count of launch i (ncu -k
+        # regex:k_search -s i -c 1) over launches[i].nodes gives instructions
+        # per expansion.
+        #   --profile-batched: all boards of the workload in one call (width
+        #   5: the 24-puzzle walks with the oracle's node budget);
+        #   --profile-case IDX: board IDX alone.
         W = args.profile_width
-        # the 24-puzzle case: a walk of the 1024-walk workload, with the
-        # oracle's node budget as in that workload
-        x = (I.walks24_1024() if W == 5 else insts)[args.profile_case]
-        b = torch.from_numpy(I.packed_array([x]).view(np.int64)).to(dev)
+        pool = I.walks24_1024() if W == 5 else insts
+        x = pool if args.profile_batched else [pool[args.profile_case]]
+        b = torch.from_numpy(I.packed_array(x).view(np.int64)).to(dev)
         budget = 50_000_000 if W == 5 else 0
+        if args.profile_variant >= 2:
+            cfg = bpida.make_config(W, variant=args.profile_variant)
+        else:
+            cfg = bpida.make_config(W, exit_fraction_pct=0 if args.profile_default else 100, driver=1,
+                                    variant=args.profile_variant, node_budget=budget)
+        log = None
         for rep in range(2):
-            # host-driven loop: ncu cannot see kernels inside graphs that
-            # hold conditional nodes
-            if args.profile_variant >= 2:
-                cfg = bpida.make_config(W, variant=args.profile_variant)
-            else:
-                cfg = bpida.make_config(W, exit_fraction_pct=0 if args.profile_default else 100, driver=1,
-                                        variant=args.profile_variant, node_budget=budget)
+            bpida.set_timing(rep == 0)
             s = bpida.solve(b, W, cfg)
             torch.cuda.synchronize(dev)
-        h = s.to_host()[0]
+            if rep == 0:
+                log = bpida.launch_log()
+        bpida.set_timing(False)
         st = bpida.last_stats()
-        print(json.dumps({"profile_case": args.profile_case, "status": s.status, "length": h["length"],
-                          "iters": h["iters"], "nodes": h["nodes"], "stats": st}), flush=True)
+        out = {"profile": "batched" if args.profile_batched else "case %d" % args.profile_case, "width": W,
+               "boards": len(x), "status": s.status, "stats": st,
+               "launches": [{"i": i, "ms": ms, "nodes": nd} for i, (ms, nd) in enumerate(log)]}
+        if args.profile_case is not None:
+            h = s.to_host()[0]
+            out.update(length=h["length"], iters=h["iters"], nodes=h["nodes"])
+        else:
+            out["nodes"] = int(s.nodes.cpu().numpy().view(np.uint64).sum())
+        if log:
+            out["largest_launch"] = max(range(len(log)), key=lambda i: log[i][1])
+        print(json.dumps(out), flush=True)
         return
 
     gold = load_golden(args.workload)

@@ -25,8 +25,11 @@
  *   - with count_all = 0 (first-solution mode, Section 6's main timing
  *     experiment) an instance stops as soon as one of its warps pops a goal:
  *     the non-final iterations' counts are unchanged, the final iteration's
- *     count is what was expanded before the stop (it depends on timing), and
- *     the solution returned is an optimal one, not necessarily the first.
+ *     count is what was expanded before the stop (it depends on timing; at
+ *     most the count_all = 1 count, which it equals when a call of at most 8
+ *     boards searched that iteration in one step with the ones before it),
+ *     and the solution returned is an optimal one, not necessarily the
+ *     first.
  *
  * Board packing (device memory, read-only to the library):
  *   W = 3 or 4: one uint64_t per board, tile at position p in bits [4p, 4p+4).
@@ -153,10 +156,10 @@ typedef struct {
 
 typedef struct {
     int steps;              /* device steps issued (all instances); a call of
-                               at most 8 boards in all-solutions mode without
-                               a node budget may search several consecutive
-                               thresholds of an instance in one step, with the
-                               same per-iteration results */
+                               at most 8 boards without a node budget may
+                               search several consecutive thresholds of an
+                               instance in one step, with the same
+                               per-iteration results */
     int passes;             /* search kernel launches */
     uint64_t records;       /* frontier records produced by the splitter */
     uint64_t handed_back;   /* stack entries handed back between passes */
@@ -324,13 +327,22 @@ void bpida_server_destroy(bpida_server *sv);
  * CUDA events on the launching stream (driver = 1 only). */
 void bpida_set_timing(int on);
 void bpida_get_stats(bpida_stats *out);
+/* The search kernel launches of this host thread's last solve call, if it
+ * ran the host-driven loop (driver = 1) with timing on: launch i took ms[i]
+ * milliseconds (CUDA events on the launching stream) and popped nodes[i]
+ * nodes. Writes the first min(count, cap) entries of each non-null array and
+ * returns the count (0 after a graph-driven call or with timing off). For
+ * turning a profiler's per-launch instruction count into instructions per
+ * expansion; not part of Algorithm 1. */
+int bpida_get_launch_log(double *ms, uint64_t *nodes, int cap);
 
-/* Fused iterations (calls of at most 8 boards in all-solutions mode without
- * a node budget search several consecutive thresholds in one step): a step
- * fuses the next thresholds while the highest of them is predicted (x8 per
- * threshold) to expand at most `nodes` nodes, divided among the call's
- * active boards. Results do not depend on it; only the number of steps and
- * the nodes searched above a board's optimum do. 0 restores the default
+/* Fused iterations (calls of at most 8 boards without a node budget search
+ * several consecutive thresholds in one step): a step fuses the next
+ * thresholds while the highest of them is predicted (x8 per threshold) to
+ * expand at most `nodes` nodes, divided among the call's active boards.
+ * All-solutions results do not depend on it; only the number of steps and
+ * the nodes searched above a board's optimum do (first-solution mode: also
+ * whether the final iteration's count is complete). 0 restores the default
  * (8e6). Process-wide; takes effect at the next call. */
 void bpida_set_fuse_nodes(uint64_t nodes);
 

@@ -23,7 +23,7 @@ BLOCK_PARALLEL, PAPER_KERNEL, PSIMPLE, PSTATICLB, PFULLLB, BPSTATIC, BLOCK_MODE 
 EXPORTS = (
     "bpida_max_len", "bpida_max_iters", "bpida_solve", "bpida_solve_ex", "bpida_set_timing",
     "bpida_set_fuse_nodes",
-    "bpida_get_stats", "bpida_release_workspace", "bpida_status_str", "bpida_solve_noalloc",
+    "bpida_get_stats", "bpida_get_launch_log", "bpida_release_workspace", "bpida_status_str", "bpida_solve_noalloc",
     "bpida_server_create", "bpida_server_submit", "bpida_server_poll", "bpida_server_in_flight",
     "bpida_server_get_stats", "bpida_server_clock", "bpida_server_set_time_slice", "bpida_server_destroy",
     "bpida_pdb_create", "bpida_pdb_destroy", "bpida_pdb_groups", "bpida_pdb_table_bytes",
@@ -142,6 +142,8 @@ def load():
         lib.bpida_set_fuse_nodes.restype = None
         lib.bpida_get_stats.argtypes = [ctypes.POINTER(Stats)]
         lib.bpida_get_stats.restype = None
+        lib.bpida_get_launch_log.argtypes = [vp, vp, ctypes.c_int]
+        lib.bpida_get_launch_log.restype = ctypes.c_int
         lib.bpida_release_workspace.argtypes = []
         lib.bpida_release_workspace.restype = None
         lib.bpida_solve_noalloc.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, vp]
@@ -207,6 +209,17 @@ def last_stats() -> dict:
     s = Stats()
     load().bpida_get_stats(ctypes.byref(s))
     return s.as_dict()
+
+
+def launch_log():
+    """[(ms, nodes)] of every search launch of this thread's last host-driven
+    call made with timing on (``set_timing(True)``, ``driver=1``)."""
+    lib = load()
+    k = lib.bpida_get_launch_log(None, None, 0)
+    ms = (ctypes.c_double * max(k, 1))()
+    nodes = (ctypes.c_uint64 * max(k, 1))()
+    lib.bpida_get_launch_log(ctypes.cast(ms, ctypes.c_void_p), ctypes.cast(nodes, ctypes.c_void_p), k)
+    return [(ms[i], int(nodes[i])) for i in range(k)]
 
 
 def release_workspace() -> None:

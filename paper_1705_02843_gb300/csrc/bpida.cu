@@ -48,6 +48,13 @@ namespace {
 
 thread_local bpida_stats g_stats;
 thread_local int g_timing = 0;
+// search launches of this thread's last host-driven call with timing on:
+// CUDA-event duration (ms) and the nodes the launch popped
+struct LaunchRec {
+    double ms;
+    uint64_t nodes;
+};
+thread_local std::vector<LaunchRec> g_launch_log;
 std::atomic<unsigned long long> g_fuse_nodes{0};  // 0: the defaults below
 std::mutex g_mu;
 
@@ -364,6 +371,7 @@ template <int W, int S, bool PDB = false>
 bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_len, uint8_t *out_moves,
                  uint64_t *out_nodes, int *out_iters, int *out_status, uint64_t *out_solutions, cudaStream_t st)
 {
+    g_launch_log.clear();
     int dev = 0;
     CK(cudaGetDevice(&dev));
     cudaError_t wse = cudaSuccess;
@@ -375,9 +383,10 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     Geometry g;
     g.n_cap = n;
     g.variant = cfg.variant;
-    // fused iterations: all-solutions mode of this kernel, no node budget,
-    // a call of at most FUSE_MAX_N boards
-    const bool fuse = cfg.variant == 0 && cfg.count_all == 1 && cfg.budget == 0 && n <= FUSE_MAX_N;
+    // fused iterations: this kernel, no node budget, a call of at most
+    // FUSE_MAX_N boards (in first-solution mode a fused step runs to
+    // completion and only an unfused step stops at the first goal)
+    const bool fuse = cfg.variant == 0 && cfg.budget == 0 && n <= FUSE_MAX_N;
     g.fuse = fuse;
     const int wpb = cfg.variant == 1 ? 1 : cfg.wpb;  // the paper's kernel: block = warp
     g.threads = wpb * 32;
@@ -563,6 +572,7 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
     CK(cudaMemcpyAsync(ws.h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     stats.launches = 2;
+    unsigned long long nodes_seen = ws.h_ctrl->search_nodes_total;
     int n_active = ws.h_ctrl->n_active;
     while (n_active > 0) {
         k_split<W, PDB><<<n_active, bsplit, 0, st>>>(d);
@@ -582,7 +592,9 @@ bpida_status run(const Settings &cfg, const uint64_t *boards, int n, int *out_le
                 float ms = 0.f;
                 CK(cudaEventElapsedTime(&ms, ws.ev0, ws.ev1));
                 stats.search_ms += ms;
+                g_launch_log.push_back({(double)ms, ws.h_ctrl->search_nodes_total - nodes_seen});
             }
+            nodes_seen = ws.h_ctrl->search_nodes_total;
             if (!ws.h_ctrl->pass_again)
                 break;
         }
@@ -809,6 +821,18 @@ bpida_status bpida_solve(const uint64_t *boards, int n, int *out_len, uint8_t *o
 }
 
 void bpida_set_timing(int on) { g_timing = on ? 1 : 0; }
+
+int bpida_get_launch_log(double *ms, uint64_t *nodes, int cap)
+{
+    const int k = (int)g_launch_log.size();
+    for (int i = 0; i < k && i < cap; ++i) {
+        if (ms)
+            ms[i] = g_launch_log[i].ms;
+        if (nodes)
+            nodes[i] = g_launch_log[i].nodes;
+    }
+    return k;
+}
 
 void bpida_set_fuse_nodes(uint64_t nodes) { g_fuse_nodes.store(nodes); }
 

@@ -710,6 +710,67 @@ template <int W> struct WarpStack<W, true> {
     }
 };
 
+// The search stack of k_search's Manhattan step (15-puzzle four-move step,
+// 24-puzzle in the blank's frame), with the layouts of WarpStack<W, false>
+// and WarpStack<W, true>, addressed through the 32-bit shared window with
+// explicit ld.shared/st.shared. A child is pushed by one predicated store
+// (put_if) and the slot index advances by the predicate, so the four moves
+// of a node run without a branch around each push. (This stack lives in
+// shared memory only: the global-memory overflow stacks keep WarpStack.)
+template <bool Wide> struct SharedStack;
+template <> struct SharedStack<false> {
+    typedef uint64_t Board;
+    static constexpr int ENTRY_BYTES = 16;
+    uint32_t e;  // shared-window address of entry 0
+    __device__ __forceinline__ void init(unsigned char *base, int) { e = (uint32_t)__cvta_generic_to_shared(base); }
+    __device__ __forceinline__ void put_if(uint32_t p, int i, uint64_t b, uint32_t meta, uint32_t org)
+    {
+        asm volatile("{ .reg .pred q; setp.ne.u32 q, %0, 0; @q st.shared.v4.u32 [%1], {%2, %3, %4, %5}; }"
+                     :: "r"(p), "r"(e + 16u * (uint32_t)i), "r"((uint32_t)b), "r"((uint32_t)(b >> 32)), "r"(meta),
+                        "r"(org) : "memory");
+    }
+    __device__ __forceinline__ void put(int i, uint64_t b, uint32_t meta, uint32_t org)
+    {
+        asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};"
+                     :: "r"(e + 16u * (uint32_t)i), "r"((uint32_t)b), "r"((uint32_t)(b >> 32)), "r"(meta), "r"(org)
+                     : "memory");
+    }
+    __device__ __forceinline__ void get(int i, uint64_t &b, uint32_t &meta, uint32_t &org) const
+    {
+        uint32_t x, y;
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(x), "=r"(y), "=r"(meta), "=r"(org) : "r"(e + 16u * (uint32_t)i) : "memory");
+        b = ((uint64_t)y << 32) | x;
+    }
+};
+template <> struct SharedStack<true> {
+    typedef u128 Board;
+    static constexpr int ENTRY_BYTES = 24;
+    uint32_t eb, em;  // shared-window addresses of board 0 and {meta, origin} 0
+    __device__ __forceinline__ void init(unsigned char *base, int S)
+    {
+        eb = (uint32_t)__cvta_generic_to_shared(base);
+        em = eb + 16u * (uint32_t)S;
+    }
+    __device__ __forceinline__ void put_if(uint32_t p, int i, u128 b, uint32_t meta, uint32_t org)
+    {
+        asm volatile("{ .reg .pred q; setp.ne.u32 q, %0, 0; @q st.shared.v4.u32 [%1], {%2, %3, %4, %5}; "
+                     "@q st.shared.v2.u32 [%6], {%7, %8}; }"
+                     :: "r"(p), "r"(eb + 16u * (uint32_t)i), "r"((uint32_t)b), "r"((uint32_t)(b >> 32)),
+                        "r"((uint32_t)(b >> 64)), "r"((uint32_t)(b >> 96)), "r"(em + 8u * (uint32_t)i), "r"(meta),
+                        "r"(org) : "memory");
+    }
+    __device__ __forceinline__ void put(int i, u128 b, uint32_t meta, uint32_t org) { put_if(1u, i, b, meta, org); }
+    __device__ __forceinline__ void get(int i, u128 &b, uint32_t &meta, uint32_t &org) const
+    {
+        uint32_t x, y, z, w;
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(x), "=r"(y), "=r"(z), "=r"(w) : "r"(eb + 16u * (uint32_t)i) : "memory");
+        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(meta), "=r"(org) : "r"(em + 8u * (uint32_t)i) : "memory");
+        b = ((u128)w << 96) | ((u128)z << 64) | ((u128)y << 32) | x;
+    }
+};
+
 // Legal blank moves of every position as one integer constant: the 4-bit
 // mask of position p (bit m = move m keeps the blank on the board) sits at
 // bit BITS*p, so the blank's field offset indexes it directly.
@@ -904,10 +965,11 @@ __global__ void k_search(const Dev<W> a)
 {
     typedef typename Geo<W>::B B;
     typedef SearchBoard<W, PDB> SB;  // what a stack entry holds (B, or the PDB pair)
-    typedef WarpStack<W, (W == 5) || PDB> Stack;
     constexpr int BITS = Geo<W>::BITS;
     constexpr bool FM = FourMoves<W, PDB>::on;           // four moves at once (15-puzzle)
     constexpr bool BF = BlankFrame<W, PDB>::on;          // boards in the blank's frame (24-puzzle)
+    typedef WarpStack<W, (W == 5) || PDB> GStack;        // layout of the overflow stacks (global memory)
+    typedef typename std::conditional<FM || BF, SharedStack<(W == 5) || PDB>, GStack>::type Stack;
     extern __shared__ __align__(16) unsigned char smem[];
     // end-of-pass bookkeeping is combined per block, so that the grid-wide
     // counters see one atomic per block instead of one per warp
@@ -952,12 +1014,14 @@ __global__ void k_search(const Dev<W> a)
     __syncthreads();
     const uint32_t one = *(volatile uint32_t *)&s_one;
     const uint32_t ebyte[4] = {one, one << 8, one << 16, one << 24};
-    const uint32_t neg4 = 0u - 4u * one;
+    // signed byte 4 in byte m: with the away bits (0x80, i.e. -128 as a
+    // signed byte) a signed dot product gives -512, the slack step of 2
+    const int e4[4] = {(int)(4u * one), (int)((4u * one) << 8), (int)((4u * one) << 16), (int)((4u * one) << 24)};
     // this warp's overflow stack in global memory: the oldest open nodes go
     // there when the shared stack is full and come back when it drains
     // (24-puzzle only: its deeper trees overflow the shared stack often)
     constexpr bool OVF = (W == 5);
-    Stack ovf;
+    GStack ovf;
     const size_t gwarp = (size_t)blockIdx.x * (blockDim.x >> 5) + warp;
     ovf.init(a.ovf + gwarp * (size_t)a.ovf_cap * Stack::ENTRY_BYTES, a.ovf_cap);
     int ovf_n = 0;
@@ -1053,7 +1117,10 @@ __global__ void k_search(const Dev<W> a)
             }
             const int J = FUSE ? acc_J : 0;
             __syncwarp();
+            // nodes popped in this run: a 32-bit count per round, folded into
+            // the 64-bit total every 32 rounds (at most 1024 in between)
             unsigned long long nodes = 0, flushed = 0;
+            unsigned n32 = 0;
 
             while (top > 0 || (OVF && ovf_n > 0)) {
                 if (OVF && top == 0) {
@@ -1114,7 +1181,7 @@ __global__ void k_search(const Dev<W> a)
                 // otherwise); the lanes past n push nothing and count nothing
                 stk.get(top - n + lane, b, mt, org);
                 top -= n;
-                nodes += (unsigned long long)n;
+                n32 += (unsigned)n;
                 __syncwarp();
 
                 // (in the blank's frame, a board whose blank is elsewhere can
@@ -1126,7 +1193,11 @@ __global__ void k_search(const Dev<W> a)
                     if (lane == 0) {
                         atomicAdd(&a.cnt.goals[inst0], (unsigned long long)__popc(gmask));
                         atomicMin(&a.cnt.goal_origin[inst0], o);
-                        if (first_only)
+                        // first-solution mode stops the instance, unless this
+                        // step fuses several of its thresholds: a fused step
+                        // runs to completion (the counts of its lower
+                        // thresholds need the whole pass)
+                        if (first_only && J == 0)
                             atomicOr(&a.cnt.aborted[inst0], ABORT_FOUND);
                     }
                     if (FUSE && J && goal) {
@@ -1190,13 +1261,14 @@ __global__ void k_search(const Dev<W> a)
                         const uint32_t clo = t * mlo[m] + (uint32_t)bq, chi = t * mhi[m] + (uint32_t)(bq >> 32);
                         const B child = ((uint64_t)chi << 32) | clo;
                         // the child's blank, its excluded move (the inverse of m)
-                        // and its slack (s - 2 when the tile moved away, else s)
-                        const uint32_t aw = (uint32_t)__dp4a(away4, ebyte[m], 0u);  // 128 when away
-                        const uint32_t cm = aw * neg4 + (keep + (uint32_t)move_off<W>(m) + (0x80u << (8 * (3 - m))));
-                        if (push4 & (0x80u << (8 * m))) {
-                            stk.put(sp, child, cm, org);
-                            ++sp;
-                        }
+                        // and its slack (s - 2 when the tile moved away, else s:
+                        // the signed dot product of the away bits with e4[m])
+                        const uint32_t cm = (uint32_t)__dp4a(
+                            (int)away4, e4[m], (int)(keep + (uint32_t)move_off<W>(m) + (0x80u << (8 * (3 - m)))));
+                        const uint32_t pb = push4 & (0x80u << (8 * m));
+                        if constexpr (FM)
+                            stk.put_if(pb, sp, child, cm, org);
+                        sp += pb ? 1 : 0;
                     }
 
                 } else if constexpr (BF) {
@@ -1260,13 +1332,13 @@ __global__ void k_search(const Dev<W> a)
                     const uint32_t keep = mt & ~(15u << 7);
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
-                        if ((push4 >> m) & 1u) {
-                            const uint32_t cm = aw[m] * (0u - (2u << 11)) +
-                                                (keep + (uint32_t)(BITS * move_off<W>(m)) + ((1u << (3 - m)) << 7));
-                            const B child = ((u128)c3[m] << 96) | ((u128)c2[m] << 64) | ((u128)c1[m] << 32) | c0[m];
-                            stk.put(sp, child, cm, org);
-                            ++sp;
-                        }
+                        const uint32_t pb = (push4 >> m) & 1u;
+                        const uint32_t cm = aw[m] * (0u - (2u << 11)) +
+                                            (keep + (uint32_t)(BITS * move_off<W>(m)) + ((1u << (3 - m)) << 7));
+                        const B child = ((u128)c3[m] << 96) | ((u128)c2[m] << 64) | ((u128)c1[m] << 32) | c0[m];
+                        if constexpr (BF)
+                            stk.put_if(pb, sp, child, cm, org);
+                        sp += (int)pb;
                     }
                 } else {
                 const uint32_t sh_p = mt & 127u;
@@ -1351,7 +1423,9 @@ __global__ void k_search(const Dev<W> a)
                 __syncwarp();
 
                 if (((++rounds) & 31) == 0) {
-                    if (first_only) {
+                    nodes += n32;
+                    n32 = 0;
+                    if (first_only && J == 0) {
                         int found = 0;
                         if (lane == 0)
                             found = (*(volatile unsigned *)&a.cnt.aborted[inst0] & ABORT_FOUND) != 0;
@@ -1396,6 +1470,7 @@ __global__ void k_search(const Dev<W> a)
                 }
             }
             // this run's counts
+            nodes += n32;
             acc_nodes += nodes - flushed;
             tot_nodes += nodes;
             if (budgeted)

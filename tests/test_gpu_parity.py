@@ -303,6 +303,27 @@ def test_graph_and_host_drivers_agree_on_batch():
     assert a == b
 
 
+def test_launch_log_of_a_host_driven_call():
+    """With timing on, a host-driven call logs every search launch: one entry
+    per pass, and the nodes of the entries add up to the nodes the search
+    kernel popped; a graph-driven call logs nothing."""
+    insts = I.walks15_16x40()
+    tiles = [x.tiles for x in insts]
+    bpida.set_timing(True)
+    try:
+        rc, got = gpu_solve(4, tiles, driver=1)
+        st = bpida.last_stats()
+        log = bpida.launch_log()
+        assert rc == bpida.OK
+        assert len(log) == st["passes"] > 0
+        assert sum(nd for _, nd in log) == st["search_nodes"]
+        assert all(ms > 0 for ms, _ in log)
+        rc, _ = gpu_solve(4, tiles, driver=0)
+        assert rc == bpida.OK and bpida.launch_log() == []
+    finally:
+        bpida.set_timing(False)
+
+
 def test_repeated_plain_calls_reuse_the_graph():
     insts = I.walks15_16x40()[:6]
     ref = oracle.solve_batch(4, np.array([x.tiles for x in insts], dtype=np.uint8))
@@ -445,6 +466,27 @@ def test_first_solution_mode_one_board_per_call():
         assert g["nodes"][:-1] == r.nodes[:-1]
         assert 1 <= g["nodes"][-1] <= r.nodes[-1]
         assert P.replay(4, t, g["moves"]) == list(range(16))
+
+
+def test_first_solution_mode_with_fused_steps():
+    """One-board calls in first-solution mode fuse small thresholds into one
+    step, and a fused step runs to completion: lengths and non-final counts
+    are the oracle's, the final count is at most the all-solutions count and
+    equals it when the final iteration was fused (small walks: here most of
+    them); every path replays."""
+    insts = I.walks15_16x40()
+    tiles = [x.tiles for x in insts]
+    ref = oracle.solve_batch(4, np.array(tiles, dtype=np.uint8), count_all=True)
+    equal = 0
+    for t, r in zip(tiles, ref):
+        rc, got = gpu_solve(4, [t], count_all=False)
+        g = got[0]
+        assert rc == bpida.OK and g["status"] == 0 and g["length"] == r.length
+        assert g["nodes"][:-1] == r.nodes[:-1]
+        assert 1 <= g["nodes"][-1] <= r.nodes[-1]
+        assert P.replay(4, t, g["moves"]) == list(range(16))
+        equal += g["nodes"][-1] == r.nodes[-1]
+    assert equal >= len(tiles) // 2
 
 
 @pytest.mark.parametrize("cap", [30000, 32000000])
