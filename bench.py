@@ -61,21 +61,28 @@ WORKLOAD_DESC = {
 }
 
 # Instructions per expansion of the search kernel (warp instructions issued
-# per node expanded, ncu smsp__inst_executed.sum / nodes of the captured
-# launches), its share on the integer ALU pipe (16 lanes per scheduler: one
-# warp instruction every 2 cycles, so above one half the ALU pipe, not issue,
-# bounds the kernel at issue peak / (2 x share)), and DRAM bytes (read +
-# write) of a captured launch, for the kernel each form runs.
-#   batched: k_search<4,480,0>, every launch of two batched solves of the
-#   4096-board mix; ALU share and DRAM bytes from one full capture
-#   (profiles/k_search_15puzzle_mixed15_4096_batched.txt);
+# per node expanded: ncu smsp__inst_executed.sum of one launch over the nodes
+# that launch popped, which the host-driven loop logs per launch), its share
+# on the integer ALU pipe (16 lanes per scheduler: one warp instruction every
+# 2 cycles, so above one half the ALU pipe, not issue, bounds the kernel at
+# issue peak / (2 x share)), and DRAM bytes (read + write) of the captured
+# launch, for the kernel each form runs.
+#   batched: k_search<4,480,0>, a steady-state launch (the first pass of a
+#   step, hand-back on) of a batched solve of the 4096-board mix: 323.4 M
+#   warp instructions over 70.7 M nodes; ALU share (issue 84.4 %, ALU pipe
+#   68.2 % busy) and DRAM bytes from one full capture of such a launch
+#   (profiles/k_search_15puzzle_mixed15_4096_batched.txt). Hand-back passes
+#   with few nodes issue more per node (4.7-5.7), so issue utilisation
+#   computed with this figure is a lower bound;
 #   plain: the fused-iteration variant k_search<4,480,1>, the final iteration
-#   of board 0 of the mix as one pass
-#   (profiles/k_search_15puzzle_plain_fused_final_iteration.txt).
+#   of board 0 of the mix as one pass (52.4 M nodes)
+#   (profiles/k_search_15puzzle_plain_fused_final_iteration.txt); its ALU
+#   share is the batched kernel's (the same step; a single-board launch's
+#   pipe fractions are skewed by its tail).
 KERNEL_COUNTERS = {
-    "batched": {"kernel": "k_search<4,480,0>", "instr_per_expansion": 4.78, "alu_pipe_share": 0.425,
-                "traffic_per_launch": 9683712},
-    "plain": {"kernel": "k_search<4,480,1>", "instr_per_expansion": 5.15, "alu_pipe_share": 0.418,
+    "batched": {"kernel": "k_search<4,480,0>", "instr_per_expansion": 4.57, "alu_pipe_share": 0.404,
+                "traffic_per_launch": 9823744},
+    "plain": {"kernel": "k_search<4,480,1>", "instr_per_expansion": 4.67, "alu_pipe_share": 0.404,
               "traffic_per_launch": None},
 }
 
@@ -515,14 +522,24 @@ def run_pdb(args):
     if args.profile_pdb is not None:
         # host-driven loop (ncu cannot see kernels inside graphs with
         # conditional nodes); -1: the batched call
+        # (with --profile-default as in the bench, else hand-back off); the
+        # first solve's search launches are printed with their node counts
         b = boards if args.profile_pdb < 0 else boards[args.profile_pdb:args.profile_pdb + 1]
-        cfg = bpida.make_config(4, driver=1)
-        for _ in range(2):
+        cfg = bpida.make_config(4, driver=1, exit_fraction_pct=0 if args.profile_default else 100)
+        log = None
+        for rep in range(2):
+            bpida.set_timing(rep == 0)
             s = bpida.solve(b, 4, cfg, pdb=pdb)
             torch.cuda.synchronize(dev)
+            if rep == 0:
+                log = bpida.launch_log()
+        bpida.set_timing(False)
         print(json.dumps({"profile_pdb": args.profile_pdb, "partition": part, "status": s.status,
                           "nodes": int(s.nodes.cpu().numpy().view(np.uint64).sum()),
-                          "stats": bpida.last_stats()}), flush=True)
+                          "stats": bpida.last_stats(),
+                          "launches": [{"i": i, "ms": ms, "nodes": nd} for i, (ms, nd) in enumerate(log)],
+                          "largest_launch": max(range(len(log)), key=lambda i: log[i][1]) if log else None}),
+              flush=True)
         return
 
     cfg = bpida.make_config(4)
@@ -937,9 +954,11 @@ def leg_perms(bpida, torch, dev, timer, steps, clocks_hint):
 
 
 # 24-puzzle search kernel k_search<5,384,0>: warp instructions per expansion
-# and ALU share of the final iteration of walk 406 of walks24_1024 (39.7M
-# nodes, one pass) (profiles/k_search_24puzzle_walk406_final_iteration.txt).
-KERNEL_COUNTERS_W5 = {"kernel": "k_search<5,384,0>", "instr_per_expansion": 9.94, "alu_pipe_share": 0.556,
+# and ALU share of the largest launch (7.25 G nodes, one pass per step) of a
+# batched solve of walks24_1024 with the 5e7 node budget
+# (profiles/k_search_24puzzle_walks24_1024_batched.txt); DRAM bytes are those
+# of that launch, not of the bench's launches (hand-back on), so none here.
+KERNEL_COUNTERS_W5 = {"kernel": "k_search<5,384,0>", "instr_per_expansion": 6.13, "alu_pipe_share": 0.42,
                       "traffic_per_launch": None}
 
 

@@ -127,7 +127,10 @@ template <int W> inline MoveLut<W> make_move_lut()
 
 // Per-lane view of one table row. W <= 4: the four 16-bit masks of a row
 // are packed into one 64-bit word, so a warp reads the 16 rows from 32
-// distinct banks. W = 5: one 16-byte row.
+// distinct banks. W = 5: a 16-byte row, held as two arrays of 8-byte halves
+// (words 0-1 of the 25 rows, then words 2-3): a half-warp's 8-byte loads of
+// one array share a bank only for positions 16 apart (16-byte rows shared
+// banks every 8 positions).
 template <int W, bool Narrow = (W <= 4)> struct LutRow;
 template <int W> struct LutRow<W, true> {
     uint64_t v;
@@ -158,22 +161,25 @@ template <int W> struct SharedLut {
             // bits 28..31 of the first word: the four legal bits again (bit
             // 28 + m: move m), so that one shift gives the position's moves
             // (tiles are at most 24: the away bits stay below)
-            uint4 *d = (uint4 *)dst;
+            uint2 *d = (uint2 *)dst;
             for (int p = threadIdx.x; p < Geo<W>::N; p += blockDim.x) {
                 uint32_t legal = 0;
                 for (int m = 0; m < 4; ++m)
                     legal |= (src.e[p][m] & 1u) << (28 + m);
-                d[p] = make_uint4(src.e[p][0] | legal, src.e[p][1], src.e[p][2], src.e[p][3]);
+                d[p] = make_uint2(src.e[p][0] | legal, src.e[p][1]);
+                d[Geo<W>::N + p] = make_uint2(src.e[p][2], src.e[p][3]);
             }
         }
     }
     __device__ static __forceinline__ LutRow<W> row(const unsigned char *base, int p)
     {
         LutRow<W> r;
-        if constexpr (W <= 4)
+        if constexpr (W <= 4) {
             r.v = ((const uint64_t *)base)[p];
-        else
-            r.v = ((const uint4 *)base)[p];
+        } else {
+            const uint2 lo = ((const uint2 *)base)[p], hi = ((const uint2 *)base)[Geo<W>::N + p];
+            r.v = make_uint4(lo.x, lo.y, hi.x, hi.y);
+        }
         return r;
     }
 };
