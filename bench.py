@@ -478,12 +478,15 @@ def run_workloads(args):
 
 
 # k_search<4,384,0,1> (the pattern-database search kernel of batched calls):
-# warp instructions issued per node expanded and DRAM bytes per launch, from
-# ncu over all its launches of two batched solves of the 100 boards
-# (profiles/k_search_pdb555_perms15_100_batched.txt); None where not measured.
-INSTR_PER_EXPANSION_PDB = {"555": 14.5, "663": 16.2}
-TRAFFIC_PER_LAUNCH_PDB = {"555": 13.8e6, "663": 62.2e6}
-ALU_PIPE_SHARE_PDB = {"555": 0.528, "663": 0.527}
+# warp instructions issued per node expanded, from ncu on the largest launch
+# of a batched solve of the 100 boards with hand-back off, over the nodes the
+# launch log records for it (profiles/k_search_pdb555_perms15_100_batched.txt).
+# DRAM bytes and the ALU share of those launches are not those of the bench's
+# launches (hand-back on; a single launch's pipe fractions are skewed by its
+# tail), so none here.
+INSTR_PER_EXPANSION_PDB = {"555": 11.32, "663": 11.48}
+TRAFFIC_PER_LAUNCH_PDB = {}
+ALU_PIPE_SHARE_PDB = {}
 
 
 def run_pdb(args):

@@ -720,20 +720,23 @@ template <int W> struct WarpStack<W, true> {
 // 24-puzzle in the blank's frame), with the layouts of WarpStack<W, false>
 // and WarpStack<W, true>, addressed through the 32-bit shared window with
 // explicit ld.shared/st.shared. A child is pushed by one predicated store
-// (put_if) and the slot index advances by the predicate, so the four moves
-// of a node run without a branch around each push. (This stack lives in
-// shared memory only: the global-memory overflow stacks keep WarpStack.)
+// (put_if) and the slot (15-puzzle: the slot's shared-window address)
+// advances by the predicate, so the four moves of a node run without a
+// branch around each push. (This stack lives in shared memory only: the
+// global-memory overflow stacks keep WarpStack.)
 template <bool Wide> struct SharedStack;
 template <> struct SharedStack<false> {
     typedef uint64_t Board;
     static constexpr int ENTRY_BYTES = 16;
     uint32_t e;  // shared-window address of entry 0
     __device__ __forceinline__ void init(unsigned char *base, int) { e = (uint32_t)__cvta_generic_to_shared(base); }
-    __device__ __forceinline__ void put_if(uint32_t p, int i, uint64_t b, uint32_t meta, uint32_t org)
+    // shared-window address of entry i
+    __device__ __forceinline__ uint32_t addr(int i) const { return e + 16u * (uint32_t)i; }
+    // stores the entry at shared-window address a if p is nonzero
+    __device__ __forceinline__ void put_if(uint32_t p, uint32_t a, uint64_t b, uint32_t meta, uint32_t org)
     {
         asm volatile("{ .reg .pred q; setp.ne.u32 q, %0, 0; @q st.shared.v4.u32 [%1], {%2, %3, %4, %5}; }"
-                     :: "r"(p), "r"(e + 16u * (uint32_t)i), "r"((uint32_t)b), "r"((uint32_t)(b >> 32)), "r"(meta),
-                        "r"(org) : "memory");
+                     :: "r"(p), "r"(a), "r"((uint32_t)b), "r"((uint32_t)(b >> 32)), "r"(meta), "r"(org) : "memory");
     }
     __device__ __forceinline__ void put(int i, uint64_t b, uint32_t meta, uint32_t org)
     {
@@ -758,6 +761,7 @@ template <> struct SharedStack<true> {
         eb = (uint32_t)__cvta_generic_to_shared(base);
         em = eb + 16u * (uint32_t)S;
     }
+    // stores entry i if p is nonzero
     __device__ __forceinline__ void put_if(uint32_t p, int i, u128 b, uint32_t meta, uint32_t org)
     {
         asm volatile("{ .reg .pred q; setp.ne.u32 q, %0, 0; @q st.shared.v4.u32 [%1], {%2, %3, %4, %5}; "
@@ -1242,12 +1246,15 @@ __global__ void k_search(const Dev<W> a)
                     const uint32_t push4 = allowed4 & ~(away4 & low4);
                     prn |= allowed4 & away4 & low4;
                     const uint32_t keep = mq & 0x7F0Fu;  // blank position and slack
-                    // slots: this lane's children go to sp, sp + 1, ... (the
-                    // prefix of the per-lane counts, from their bit-sliced ballots)
+                    // slots: this lane's children go to consecutive entries from
+                    // base + the prefix of the per-lane counts (from their
+                    // bit-sliced ballots); sa is the next one's shared-window address
                     const unsigned c = __popc(push4);
                     const unsigned B0 = __ballot_sync(FULL, c & 1u), B1 = __ballot_sync(FULL, c & 2u),
                                    B2 = __ballot_sync(FULL, c & 4u);
-                    int sp = base + __popc(B0 & lt) + 2 * __popc(B1 & lt) + 4 * __popc(B2 & lt);
+                    uint32_t sa = 0;
+                    if constexpr (FM)
+                        sa = stk.addr(base + __popc(B0 & lt) + 2 * __popc(B1 & lt) + 4 * __popc(B2 & lt));
                     base += (int)__reduce_add_sync(FULL, c);
                     // the children: move m writes its tile t into the blank's field
                     // (zero) and clears the neighbour's (which holds t), i.e. adds t
@@ -1273,8 +1280,8 @@ __global__ void k_search(const Dev<W> a)
                             (int)away4, e4[m], (int)(keep + (uint32_t)move_off<W>(m) + (0x80u << (8 * (3 - m)))));
                         const uint32_t pb = push4 & (0x80u << (8 * m));
                         if constexpr (FM)
-                            stk.put_if(pb, sp, child, cm, org);
-                        sp += pb ? 1 : 0;
+                            stk.put_if(pb, sa, child, cm, org);
+                        sa += pb ? 16u : 0u;
                     }
 
                 } else if constexpr (BF) {

@@ -77,8 +77,10 @@ def test_instance_ranges_partition_the_workload(n, world):
 
 
 def test_bench_pattern_database_constants_cover_every_partition():
-    """Every tile partition the --pdb leg accepts has its measured kernel
-    figures, and the command line offers exactly those partitions."""
+    """Every tile partition the --pdb leg accepts has its measured
+    instructions per expansion (DRAM bytes and ALU share only where measured
+    on the bench's own launches), and the command line offers exactly those
+    partitions."""
     import subprocess
     import sys
 
@@ -86,8 +88,9 @@ def test_bench_pattern_database_constants_cover_every_partition():
     from paper_1705_02843_gb300 import inputs as I
 
     parts = set(I.PDB_PARTITIONS)
+    assert set(bench.INSTR_PER_EXPANSION_PDB) == parts
     for table in (bench.INSTR_PER_EXPANSION_PDB, bench.TRAFFIC_PER_LAUNCH_PDB, bench.ALU_PIPE_SHARE_PDB):
-        assert set(table) == parts
+        assert set(table) <= parts
         assert all(v is not None and v > 0 for v in table.values())
     for form in ("batched", "plain"):
         k = bench.KERNEL_COUNTERS[form]
