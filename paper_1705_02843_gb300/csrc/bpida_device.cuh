@@ -1060,6 +1060,18 @@ __global__ void k_search(const Dev<W> a)
     if (FUSE && lane == 0)
         for (int m = 0; m < FUSE_MAX; ++m)
             lowc[m] = 0;
+    // per lane, between flushes into lowc (every 32 rounds and at the end of
+    // a run): byte m counts this lane's pops with slack 2m, m < J (at most 32
+    // per byte between flushes)
+    unsigned long long lowp = 0;
+    auto flush_low = [&](int J) {
+        for (int m = 0; m < J; ++m) {
+            const unsigned c = __reduce_add_sync(FULL, (unsigned)(lowp >> (8 * m)) & 255u);
+            if (lane == 0)
+                lowc[m] += c;
+        }
+        lowp = 0;
+    };
     auto publish = [&]() {
         if (FM && prn)
             fmin = min(fmin, 2);
@@ -1223,11 +1235,9 @@ __global__ void k_search(const Dev<W> a)
                 const int s = FM ? (int)((mt >> 8) & 127u) : (int)((mt >> 11) & 255u);
                 if (FUSE && J) {
                     // popped nodes above the lower limits of the step
-                    for (int m = 0; m < J; ++m) {
-                        const unsigned c = __popc(__ballot_sync(FULL, act && s == 2 * m));
-                        if (lane == 0)
-                            lowc[m] += c;
-                    }
+                    const unsigned hm = (unsigned)s >> 1;
+                    if (act && hm < (unsigned)J)
+                        lowp += 1ull << (8 * hm);
                 }
                 if constexpr (FM) {
                     // the four moves at once (see FourMoves)
@@ -1438,6 +1448,8 @@ __global__ void k_search(const Dev<W> a)
                 if (((++rounds) & 31) == 0) {
                     nodes += n32;
                     n32 = 0;
+                    if (FUSE && J)
+                        flush_low(J);
                     if (first_only && J == 0) {
                         int found = 0;
                         if (lane == 0)
@@ -1484,6 +1496,8 @@ __global__ void k_search(const Dev<W> a)
             }
             // this run's counts
             nodes += n32;
+            if (FUSE && J)
+                flush_low(J);
             acc_nodes += nodes - flushed;
             tot_nodes += nodes;
             if (budgeted)
