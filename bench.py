@@ -82,7 +82,7 @@ WORKLOAD_DESC = {
 KERNEL_COUNTERS = {
     "batched": {"kernel": "k_search<4,480,0>", "instr_per_expansion": 4.50, "alu_pipe_share": 0.411,
                 "traffic_per_launch": 8110336},
-    "plain": {"kernel": "k_search<4,480,1>", "instr_per_expansion": 4.67, "alu_pipe_share": 0.411,
+    "plain": {"kernel": "k_search<4,480,1>", "instr_per_expansion": 4.72, "alu_pipe_share": 0.411,
               "traffic_per_launch": None},
 }
 
