@@ -67,22 +67,22 @@ WORKLOAD_DESC = {
 # 2 cycles, so above one half the ALU pipe, not issue, bounds the kernel at
 # issue peak / (2 x share)), and DRAM bytes (read + write) of the captured
 # launch, for the kernel each form runs.
-#   batched: k_search<4,480,0>, a steady-state launch (the first pass of a
-#   step, hand-back on) of a batched solve of the 4096-board mix: 322.5 M
-#   warp instructions over 71.6 M nodes; ALU share (issue 81.4 %, ALU pipe
-#   66.9 % busy) and DRAM bytes from one full capture of such a launch
+#   batched: k_search<4,384,0>, a steady-state launch (the first pass of a
+#   step, hand-back on) of a batched solve of the 4096-board mix: 364.6 M
+#   warp instructions over 80.8 M nodes; ALU share (issue 84.9 %, ALU pipe
+#   68.6 % busy) and DRAM bytes from one full capture of such a launch
 #   (profiles/k_search_15puzzle_mixed15_4096_batched.txt). Hand-back passes
-#   with few nodes issue more per node (4.6-5.7), so issue utilisation
+#   with few nodes issue more per node (4.7-5.8), so issue utilisation
 #   computed with this figure is a lower bound;
-#   plain: the fused-iteration variant k_search<4,480,1>, the final iteration
-#   of board 0 of the mix as one pass (52.4 M nodes)
+#   plain: the fused-iteration variant k_search<4,384,1>, the final iteration
+#   of board 0 of the mix as one pass
 #   (profiles/k_search_15puzzle_plain_fused_final_iteration.txt); its ALU
 #   share is the batched kernel's (the same step; a single-board launch's
 #   pipe fractions are skewed by its tail).
 KERNEL_COUNTERS = {
-    "batched": {"kernel": "k_search<4,480,0>", "instr_per_expansion": 4.50, "alu_pipe_share": 0.411,
-                "traffic_per_launch": 8110336},
-    "plain": {"kernel": "k_search<4,480,1>", "instr_per_expansion": 4.72, "alu_pipe_share": 0.411,
+    "batched": {"kernel": "k_search<4,384,0>", "instr_per_expansion": 4.51, "alu_pipe_share": 0.404,
+                "traffic_per_launch": 10366208},
+    "plain": {"kernel": "k_search<4,384,1>", "instr_per_expansion": 4.72, "alu_pipe_share": 0.404,
               "traffic_per_launch": None},
 }
 

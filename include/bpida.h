@@ -98,8 +98,11 @@ typedef struct {
     int split_target;     /* max frontier records per instance; 0 = auto */
     int warps_per_block;  /* search kernel block size in warps; 0 = auto */
     int stack_entries;    /* per-warp shared-memory stack, 0 = auto
-                             (width 4: 480, 5: 384, 3: 512); one of 256,
-                             384, 480, 512, 768, 1024 */
+                             (width 4 and 5: 384, 3: 512); one of 256,
+                             384, 480, 512, 768, 1024. Smaller stacks
+                             spill to the hand-back queue more often: with
+                             256 a batch of hard boards can overflow it
+                             (those instances end with BPIDA_ENOMEM) */
     int exit_fraction_pct;/* percentage of warps that must have run out of
                              work before busy warps hand their stacks back
                              for redistribution; 0 = auto */

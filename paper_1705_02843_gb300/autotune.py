@@ -39,14 +39,14 @@ KNOBS = {
     "min_rounds": [32, 64, 128],
 }
 # The library's defaults (bpida.cu) for each width.
-DEFAULT = {"variant": 0, "split_target": 4096, "warps_per_block": 4, "stack_entries": 480,
+DEFAULT = {"variant": 0, "split_target": 4096, "warps_per_block": 4, "stack_entries": 384,
            "exit_fraction_pct": 10, "min_rounds": 64}
 
 
 def defaults(width: int) -> Dict[str, int]:
     d = dict(DEFAULT)
-    if width != 4:
-        d["stack_entries"] = 384 if width == 5 else 512
+    if width == 3:
+        d["stack_entries"] = 512
     return d
 
 

@@ -689,11 +689,11 @@ bpida_status parse_settings(const bpida_config *cfg_in, int n, Settings &cfg)
     cfg.count_all = cfg_in ? cfg_in->count_all : 1;
     cfg.split_target = cfg_in ? cfg_in->split_target : 0;
     cfg.wpb = (cfg_in && cfg_in->warps_per_block > 0) ? cfg_in->warps_per_block : 4;
-    // more resident warps outweigh the extra stack spills: 15-puzzle 480
-    // entries (seven 4-warp search blocks per SM), 24-puzzle 384 (24-byte
+    // more resident warps outweigh the extra stack spills: 15-puzzle 384
+    // entries (eight 4-warp search blocks per SM), 24-puzzle 384 (24-byte
     // entries); 8-puzzle 512
     cfg.S = (cfg_in && cfg_in->stack_entries > 0) ? cfg_in->stack_entries
-                                                  : (cfg.width == 4 ? 480 : cfg.width == 5 ? 384 : 512);
+                                                  : (cfg.width == 3 ? 512 : 384);
     cfg.exit_pct = (cfg_in && cfg_in->exit_fraction_pct > 0) ? cfg_in->exit_fraction_pct : 10;
     cfg.min_rounds = (cfg_in && cfg_in->min_rounds > 0) ? cfg_in->min_rounds : 64;
     cfg.driver = cfg_in ? cfg_in->driver : 0;

@@ -35,7 +35,7 @@ using namespace bp;
 namespace {
 
 constexpr int SV_W = 4;
-constexpr int SV_S = 480;
+constexpr int SV_S = 384;
 constexpr int SV_WPB = 4;
 constexpr int SV_MAXLEN = Geo<SV_W>::MAXLEN;
 constexpr int SV_MAXIT = Geo<SV_W>::MAXIT;
