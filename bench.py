@@ -26,8 +26,10 @@ node budget), ``serving`` (the continuous-batching service under Poisson
 arrivals) and ``first_solution`` (first-solution mode against the oracle's
 first-solution mode on one host core, the paper's headline comparison).
 
-Multi-GPU: instances are independent, so each rank solves its own copy of
-the workload with no collective on the data path (replicas; weak scaling).
+Multi-GPU: instances are independent, so each rank solves a contiguous range
+of the boards with no collective on the data path, and the result rows are
+gathered after the timed steps (strong scaling: the job is the workload);
+``--replicas`` has every rank solve the whole workload instead (weak scaling).
 
 ``--impl reference`` times the CPU oracle (plain sequential IDA*, one thread
 per instance, all host cores) on a bounded sample of the same workload.
@@ -82,7 +84,7 @@ WORKLOAD_DESC = {
 KERNEL_COUNTERS = {
     "batched": {"kernel": "k_search<4,384,0>", "instr_per_expansion": 4.51, "alu_pipe_share": 0.404,
                 "traffic_per_launch": 10366208},
-    "plain": {"kernel": "k_search<4,384,1>", "instr_per_expansion": 4.72, "alu_pipe_share": 0.404,
+    "plain": {"kernel": "k_search<4,384,1>", "instr_per_expansion": 4.76, "alu_pipe_share": 0.404,
               "traffic_per_launch": None},
 }
 
