@@ -486,7 +486,7 @@ def run_workloads(args):
 # DRAM bytes and the ALU share of those launches are not those of the bench's
 # launches (hand-back on; a single launch's pipe fractions are skewed by its
 # tail), so none here.
-INSTR_PER_EXPANSION_PDB = {"555": 11.32, "663": 11.48}
+INSTR_PER_EXPANSION_PDB = {"555": 13.0, "663": 13.18}
 TRAFFIC_PER_LAUNCH_PDB = {}
 ALU_PIPE_SHARE_PDB = {}
 

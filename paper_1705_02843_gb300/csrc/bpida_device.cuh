@@ -516,18 +516,34 @@ __device__ __forceinline__ int pdb_h(const PdbDev &d, const PdbInfo &pi, uint64_
         *vb = bits;
     return h;
 }
-// Whether sliding the tile at np into the blank at p raises h (else it
-// lowers h by 1); inv is the parent's inverse board.
-__device__ __forceinline__ bool pdb_away(const PdbDev &d, const PdbInfo &pi, uint64_t inv, uint32_t p, uint32_t np,
-                                         unsigned tile)
+// For each move m whose bit is set in legal: whether sliding the tile at
+// np[m] into the blank at p raises h (bit m of the result; else h falls by
+// 1); inv is the parent's inverse board. The eight table reads (the moved
+// tile's group entry of child and parent, per move) are issued before any
+// of them is used, so that their latencies overlap.
+__device__ __forceinline__ unsigned pdb_away4(const PdbDev &d, const PdbInfo &pi, uint64_t inv, uint32_t p,
+                                              const uint32_t np[4], const unsigned tile[4], unsigned legal)
 {
-    const uint32_t j = pi.slot_of_tile[tile];
-    const PdbSlot sl = pi.slot[j];
-    const uint64_t dd = (uint64_t)(p ^ np);
-    const uint64_t child = inv ^ (dd << (4 * j)) ^ dd;
-    const unsigned char *t = d.tab + sl.base;
-    const uint32_t gbits = (uint32_t)__popc(sl.mask);
-    return t[pdb_index(child, sl.goff, gbits)] > t[pdb_index(inv, sl.goff, gbits)];
+    unsigned vc[4], vp[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        vc[m] = vp[m] = 0;
+        if ((legal >> m) & 1u) {
+            const uint32_t j = pi.slot_of_tile[tile[m]];
+            const PdbSlot sl = pi.slot[j];
+            const uint64_t dd = (uint64_t)(p ^ np[m]);
+            const uint64_t child = inv ^ (dd << (4 * j)) ^ dd;
+            const unsigned char *t = d.tab + sl.base;
+            const uint32_t gbits = (uint32_t)__popc(sl.mask);
+            vc[m] = t[pdb_index(child, sl.goff, gbits)];
+            vp[m] = t[pdb_index(inv, sl.goff, gbits)];
+        }
+    }
+    unsigned away = 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+        away |= (vc[m] > vp[m] ? 1u : 0u) << m;
+    return away;
 }
 
 // ---- warp stack entries ----
@@ -1233,10 +1249,10 @@ __global__ void k_search(const Dev<W> a)
                 }
                 int base = top;
                 const int s = FM ? (int)((mt >> 8) & 127u) : (int)((mt >> 11) & 255u);
-                if (FUSE && J) {
+                if constexpr (FUSE) {
                     // popped nodes above the lower limits of the step
                     const unsigned hm = (unsigned)s >> 1;
-                    if (act && hm < (unsigned)J)
+                    if (J && act && hm < (unsigned)J)
                         lowp += 1ull << (8 * hm);
                 }
                 if constexpr (FM) {
@@ -1377,28 +1393,40 @@ __global__ void k_search(const Dev<W> a)
                     const uint64_t sb = (uint64_t)b, inv = (uint64_t)(b >> 64);
                     const uint32_t vkeep = mt & PDB_VMASK;
                     bool bad = false;
+                    // first the four table reads, issued together so that their
+                    // latencies overlap (the search waits on them, not on issue),
+                    // then the children
+                    uint32_t jm[4], vm[4];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const uint32_t sh_np = sh_p + (uint32_t)(4 * move_off<W>(m));
+                        // slot of the tile that slides into the blank (an off-board
+                        // offset reads slot 0, whose entry is zero)
+                        jm[m] = BoardOps<W>::tile(sb, sh_np);
+                        vm[m] = 0;
+                        if ((allowed >> m) & 1u) {
+                            const PdbSlot sl = pi->slot[jm[m]];
+                            // the tile moves np -> p, the blank p -> np
+                            const uint64_t dd = (uint64_t)((sh_p ^ sh_np) >> 2);
+                            const uint64_t cinv = inv ^ (dd << (4 * jm[m])) ^ dd;
+                            uint64_t f;
+                            asm("shr.b64 %0, %1, %2;" : "=l"(f) : "l"(cinv), "r"(sl.goff));
+                            // field | np << width, as one multiply-add (the field is below mask + 1)
+                            const uint32_t idx = ((uint32_t)f & sl.mask) + (sh_np >> 2) * (sl.mask + 1u);
+                            vm[m] = __ldg(a.pdb.tab + sl.base + idx);
+                        }
+                    }
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
                         const bool legal = (allowed >> m) & 1u;
                         const uint32_t sh_np = sh_p + (uint32_t)(4 * move_off<W>(m));
-                        const uint32_t np = sh_np >> 2;
-                        // slot of the tile that slides into the blank (an off-board
-                        // offset reads slot 0, whose entry is zero)
-                        const uint32_t j = BoardOps<W>::tile(sb, sh_np);
+                        const uint32_t j = jm[m];
                         const PdbSlot sl = pi->slot[j];
-                        // the tile moves np -> p, the blank p -> np
                         const uint64_t dd = (uint64_t)((sh_p ^ sh_np) >> 2);
                         const uint64_t cinv = inv ^ (dd << (4 * j)) ^ dd;
                         const uint32_t sh_q = (m < 2) ? sh_np : sh_p;  // lower of the two fields
                         const uint64_t csb = BoardOps<W>::flip(sb, j * move_mul<W>(m), sh_q);
-                        uint32_t v = 0;
-                        if (legal) {
-                            uint64_t f;
-                            asm("shr.b64 %0, %1, %2;" : "=l"(f) : "l"(cinv), "r"(sl.goff));
-                            // field | np << width, as one multiply-add (the field is below mask + 1)
-                            const uint32_t idx = ((uint32_t)f & sl.mask) + np * (sl.mask + 1u);
-                            v = __ldg(a.pdb.tab + sl.base + idx);
-                        }
+                        const uint32_t v = vm[m];
                         const uint32_t vold = mt >> sl.vsh;
                         // h_g rose by 1 (dv = 1) or fell by 1 (dv = 3); any other
                         // dv is an inconsistent table: it counts as a rise (so a
@@ -2157,9 +2185,21 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split(const Dev<W> a)
                         atomicAdd(&s_low[s >> 1], 1u);
                     const uint32_t d = m_hi(r.meta);
                     const LutRow<W> e = SharedLut<W>::row(lut, p);
-                    uint64_t inv = 0;
-                    if constexpr (PDB)
-                        inv = pdb_inverse<W>(r.b, *pi);
+                    unsigned away4 = 0;
+                    if constexpr (PDB) {
+                        // the four moves' table reads together (see pdb_away4)
+                        const uint64_t inv = pdb_inverse<W>(r.b, *pi);
+                        uint32_t npm[4];
+                        unsigned tm[4], legal = 0;
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            const bool ok = e.legal(m) && last != 3 - m;
+                            npm[m] = (uint32_t)(ok ? p + move_off<W>(m) : p);
+                            tm[m] = ok ? tile_at<W>(r.b, (int)npm[m]) : 0u;
+                            legal |= (ok ? 1u : 0u) << m;
+                        }
+                        away4 = pdb_away4(a.pdb, *pi, inv, (uint32_t)p, npm, tm, legal);
+                    }
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
                         if (!e.legal(m) || last == 3 - m)
@@ -2168,7 +2208,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split(const Dev<W> a)
                         const unsigned t = tile_at<W>(r.b, np);
                         bool away;
                         if constexpr (PDB)
-                            away = pdb_away(a.pdb, *pi, inv, (uint32_t)p, (uint32_t)np, t);
+                            away = (away4 >> m) & 1u;
                         else
                             away = e.away(m, t);
                         const int s2 = away ? s - 2 : s;
