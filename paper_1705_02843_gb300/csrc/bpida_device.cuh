@@ -1049,7 +1049,7 @@ __global__ void k_search(const Dev<W> a)
     constexpr bool OVF = (W == 5);
     GStack ovf;
     const size_t gwarp = (size_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    ovf.init(a.ovf + gwarp * (size_t)a.ovf_cap * Stack::ENTRY_BYTES, a.ovf_cap);
+    ovf.init(a.ovf + gwarp * (size_t)a.ovf_cap * GStack::ENTRY_BYTES, a.ovf_cap);
     int ovf_n = 0;
     const unsigned lt = (1u << lane) - 1u;
     const SB GOAL = search_goal<W, PDB>(a);
