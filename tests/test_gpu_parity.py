@@ -324,6 +324,25 @@ def test_launch_log_of_a_host_driven_call():
         bpida.set_timing(False)
 
 
+def test_small_stacks_report_queue_overflow_not_wrong_results():
+    """A 256-entry stack spills so often on the 100 random permutations in
+    one batched call that the hand-back queue overflows: the instances it
+    hits end with BPIDA_ENOMEM, and every instance that ends with BPIDA_OK
+    has the oracle's exact results."""
+    doc = _golden("perms15_100")
+    gold = {r["index"]: r for r in doc["instances"]}
+    tiles = [x.tiles for x in I.perms15_100()]
+    rc, got = gpu_solve(4, tiles, stack_entries=256)
+    assert rc == bpida.OK
+    statuses = {g["status"] for g in got}
+    assert statuses <= {bpida.OK, bpida.ENOMEM}
+    for i, g in enumerate(got):
+        if g["status"] == bpida.OK:
+            r = gold[i]
+            assert g["length"] == r["length"] and g["nodes"] == r["nodes"], i
+            assert "".join(map(str, g["moves"])) == r["moves"], i
+
+
 def test_repeated_plain_calls_reuse_the_graph():
     insts = I.walks15_16x40()[:6]
     ref = oracle.solve_batch(4, np.array([x.tiles for x in insts], dtype=np.uint8))
