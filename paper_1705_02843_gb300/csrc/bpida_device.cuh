@@ -1147,6 +1147,14 @@ __global__ void k_search(const Dev<W> a)
                     stk.put(lane, r.b, FM ? fm_from_rec(r.meta) : sm_from_rec<W>(r.meta), r.origin);
                 }
             }
+            if constexpr (FM || BF) {
+                // the slots of these steps assume at most three children per
+                // node: a record without a parent move (only the goal can be
+                // one, the splitter expands every other root) fails the call
+                const bool root = lane < cnt && !dropped && m_last(r.meta) == LAST_NONE && r.b != GOAL;
+                if (__any_sync(FULL, root) && lane == 0)
+                    atomicOr(&a.ctrl->err, ERR_INTERNAL);
+            }
             int top = dropped ? 0 : cnt;
             if (inst0 != acc_inst) {
                 publish();
@@ -1275,12 +1283,12 @@ __global__ void k_search(const Dev<W> a)
                     // slots: this lane's children go to consecutive entries from
                     // base + the prefix of the per-lane counts (from their
                     // bit-sliced ballots); sa is the next one's shared-window address
+                    // (every node here has a parent move, so c <= 3: two slices)
                     const unsigned c = __popc(push4);
-                    const unsigned B0 = __ballot_sync(FULL, c & 1u), B1 = __ballot_sync(FULL, c & 2u),
-                                   B2 = __ballot_sync(FULL, c & 4u);
+                    const unsigned B0 = __ballot_sync(FULL, c & 1u), B1 = __ballot_sync(FULL, c & 2u);
                     uint32_t sa = 0;
                     if constexpr (FM)
-                        sa = stk.addr(base + __popc(B0 & lt) + 2 * __popc(B1 & lt) + 4 * __popc(B2 & lt));
+                        sa = stk.addr(base + __popc(B0 & lt) + 2 * __popc(B1 & lt));
                     base += (int)__reduce_add_sync(FULL, c);
                     // the children: move m writes its tile t into the blank's field
                     // (zero) and clears the neighbour's (which holds t), i.e. adds t
@@ -1336,9 +1344,9 @@ __global__ void k_search(const Dev<W> a)
                     // slots: this lane's children go to sp, sp + 1, ... (the
                     // prefix of the per-lane counts, from their bit-sliced ballots)
                     const unsigned c = __popc(push4);
-                    const unsigned B0 = __ballot_sync(FULL, c & 1u), B1 = __ballot_sync(FULL, c & 2u),
-                                   B2 = __ballot_sync(FULL, c & 4u);
-                    int sp = base + __popc(B0 & lt) + 2 * __popc(B1 & lt) + 4 * __popc(B2 & lt);
+                    // (every node here has a parent move, so c <= 3: two slices)
+                    const unsigned B0 = __ballot_sync(FULL, c & 1u), B1 = __ballot_sync(FULL, c & 2u);
+                    int sp = base + __popc(B0 & lt) + 2 * __popc(B1 & lt);
                     base += (int)__reduce_add_sync(FULL, c);
                     // the children: the board turned left by 25 (up) or 5 bits
                     // (left), right by 5 (right) or 25 (down); field 0 then holds
@@ -2151,7 +2159,10 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split(const Dev<W> a)
         int expandable = (st.root == GOAL) ? 0 : 1;
         Rec<W> *cur = lvl[0];
         for (;;) {
-            if (cnt >= T || depth >= 16 || 4 * cnt > a.C || expandable == 0)
+            // the root is always expanded here (unless it is the goal): every
+            // record the search kernel receives then has a parent move, so a
+            // node there has at most three children
+            if (expandable == 0 || depth >= 16 || 4 * cnt > a.C || (depth > 0 && cnt >= T))
                 break;
             // the next level has at most 4*cnt records: shared memory if they fit
             Rec<W> *nxt;
