@@ -70,11 +70,11 @@ WORKLOAD_DESC = {
 # issue peak / (2 x share)), and DRAM bytes (read + write) of the captured
 # launch, for the kernel each form runs.
 #   batched: k_search<4,384,0>, a steady-state launch (the first pass of a
-#   step, hand-back on) of a batched solve of the 4096-board mix: 364.6 M
-#   warp instructions over 80.8 M nodes; ALU share (issue 84.9 %, ALU pipe
-#   68.6 % busy) and DRAM bytes from one full capture of such a launch
+#   step, hand-back on) of a batched solve of the 4096-board mix: 331.2 M
+#   warp instructions over 77.2 M nodes; ALU share (issue 84.0 %, ALU pipe
+#   64.9 % busy) and DRAM bytes from one full capture of such a launch
 #   (profiles/k_search_15puzzle_mixed15_4096_batched.txt). Hand-back passes
-#   with few nodes issue more per node (4.7-5.8), so issue utilisation
+#   with few nodes issue more per node (4.4-5.4), so issue utilisation
 #   computed with this figure is a lower bound;
 #   plain: the fused-iteration variant k_search<4,384,1>, the final iteration
 #   of board 0 of the mix as one pass
@@ -82,9 +82,9 @@ WORKLOAD_DESC = {
 #   share is the batched kernel's (the same step; a single-board launch's
 #   pipe fractions are skewed by its tail).
 KERNEL_COUNTERS = {
-    "batched": {"kernel": "k_search<4,384,0>", "instr_per_expansion": 4.51, "alu_pipe_share": 0.404,
-                "traffic_per_launch": 10366208},
-    "plain": {"kernel": "k_search<4,384,1>", "instr_per_expansion": 4.76, "alu_pipe_share": 0.404,
+    "batched": {"kernel": "k_search<4,384,0>", "instr_per_expansion": 4.29, "alu_pipe_share": 0.386,
+                "traffic_per_launch": 10233088},
+    "plain": {"kernel": "k_search<4,384,1>", "instr_per_expansion": 4.66, "alu_pipe_share": 0.386,
               "traffic_per_launch": None},
 }
 
@@ -963,7 +963,7 @@ def leg_perms(bpida, torch, dev, timer, steps, clocks_hint):
 # batched solve of walks24_1024 with the 5e7 node budget
 # (profiles/k_search_24puzzle_walks24_1024_batched.txt); DRAM bytes are those
 # of that launch, not of the bench's launches (hand-back on), so none here.
-KERNEL_COUNTERS_W5 = {"kernel": "k_search<5,384,0>", "instr_per_expansion": 6.13, "alu_pipe_share": 0.42,
+KERNEL_COUNTERS_W5 = {"kernel": "k_search<5,384,0>", "instr_per_expansion": 5.91, "alu_pipe_share": 0.42,
                       "traffic_per_launch": None}
 
 
