@@ -1176,11 +1176,12 @@ def main():
         # for ncu: two solves through the host-driven loop (ncu cannot see
         # kernels inside graphs that hold conditional nodes), by default with
         # hand-back off (one search pass per step, plus passes for stack
-        # overflows: the launch sequence is the same in every run); the first
-        # solve's search launches are printed with their durations and node
-        # counts, so that a profiler's instruction count of launch i (ncu -k
-        # regex:k_search -s i -c 1) over launches[i].nodes gives instructions
-        # per expansion.
+        # overflows); the first solve's search launches are printed with
+        # their durations and node counts, so that a profiler's instruction
+        # count of launch i (ncu -k regex:k_search -s i -c 1) over the nodes
+        # that the same run prints for launch i gives instructions per
+        # expansion (the launch sequence can differ between runs where
+        # passes end by timing, so take both from one run).
         #   --profile-batched: all boards of the workload in one call (width
         #   5: the 24-puzzle walks with the oracle's node budget);
         #   --profile-case IDX: board IDX alone.
